@@ -1,0 +1,575 @@
+/*
+ * llr_oracle.c -- plain FP64 reference implementation ("oracle") of the
+ * window-restricted Monte Carlo of the LLR density-of-states method for
+ * compact U(1) lattice gauge theory.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline timing of the benchmark may load this library.  The product
+ * (the CUDA library under paper_1509_08391_gb300/) shares no code with it.
+ *
+ * Paper: K. Langfeld, B. Lucini, R. Pellegrini, A. Rago, "An efficient
+ * algorithm for numerical computations of continuous densities of states"
+ * (arXiv:1509.08391).  Equations are cited by the labels of the paper's
+ * source, e.g. "eq. kk21" is the under-relaxed Robbins-Monro update of
+ * Sec. 2.2.
+ *
+ * What is computed (and where it is defined):
+ *   - Sec. 3.1: link angles theta_mu(x) in [-pi,pi), plaquette angle
+ *     theta_munu(x) = theta_mu(x) + theta_nu(x+mu) - theta_mu(x+nu) - theta_nu(x),
+ *     energy E = sum_{x, mu<nu} cos theta_munu(x) (beta factored out), Haar
+ *     measure prod dtheta/2pi.
+ *   - Sec. 2.2, eqs. kk7-kk10: expectation values restricted to the closed
+ *     window E_k <= E <= E_k + dE, reweighted by exp(-a E).
+ *   - Sec. 2.4, Algorithm 1: N_TH + N_SW importance-sampling sweeps per
+ *     Robbins-Monro iteration, measuring E after N_TH, then the update of a.
+ *   - Sec. 2.2, eq. kk21: a <- a + 12 <<dE>> / (dE^2 (n+1)) (sign of kk21;
+ *     Algorithm 1 prints the opposite sign, see the readings below).
+ *
+ * Readings where the paper is silent (each one is also listed in the design doc):
+ *   R1 update scheme: the paper names only "an importance sampling
+ *      algorithm for one sweep" (Algorithm 1) and mentions heat-bath and
+ *      Metropolis.  A composite sweep here is one heat-bath pass followed by
+ *      n_or overrelaxation passes.  A pass visits the 2*d checkerboard
+ *      classes (direction mu, site parity p) in the order mu = 0..d-1,
+ *      p = 0,1; links of one class share no plaquette.
+ *   R2 window restriction (Sec. 2.4 allows imposing it after the proposal):
+ *      within a class every link draws an independent proposal from its
+ *      unrestricted conditional distribution (heat-bath at weight exp(-aE),
+ *      or the overrelaxation reflection); the proposals are then accepted
+ *      or rejected in ascending site order, in blocks of B consecutive
+ *      links, by the Metropolis rule for the restricted measure: a block is
+ *      accepted iff dist(E + dE_block) <= dist(E), where dist is the distance
+ *      of E from the window (0 inside).  Inside the window this is exactly
+ *      the indicator of eq. kk7; outside it only lets E move towards the
+ *      window (used while approaching the window from a hot start).
+ *   R3 heat-bath proposal: von Mises variate by Best & Fisher (1979).
+ *   R4 random numbers: Philox4x32-10 (Salmon et al., SC'11), one call per
+ *      sampler attempt, keyed by (seed, interval, replica), counter
+ *      (link, sweep, tag, attempt).
+ *   R5 approach phase: from a hot start, heat-bath at a = -beta_up (E below
+ *      the window) or a = -beta_dn (E above) with the dist rule, until the
+ *      energy lies in the window at the end of a composite sweep.
+ *   R6 the tracked energy is re-synchronised with a fresh plaquette sum at
+ *      the end of every composite sweep; the measurement uses that value.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11): 10 rounds of a multiply-xor bijection on a
+ * 128-bit counter, with a Weyl-sequence key schedule.
+ * ---------------------------------------------------------------------- */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += PHILOX_W0; k1 += PHILOX_W1; }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* A 32-bit word to a uniform in the open interval (0,1): the top 23 bits
+ * k give (2k+1) * 2^-24, exact in both float and double. */
+double orc_uniform(uint32_t w)
+{
+    return (double)((w >> 9) * 2u + 1u) * (1.0 / 16777216.0);
+}
+
+/* Wrap an angle to [-pi, pi). */
+static double wrap_angle(double t)
+{
+    return t - 2.0 * M_PI * floor((t + M_PI) / (2.0 * M_PI));
+}
+
+/* ------------------------------------------------------------------------
+ * Geometry: a d-dimensional hypercubic lattice (d <= 4), periodic or open.
+ * Sites are numbered lexicographically with x_0 fastest.  Link slot
+ * l = mu * nsite + site (a slot exists only if the link does, which always
+ * holds with periodic boundaries).  Plaquettes are listed explicitly from
+ * the definition of Sec. 3.1, and every link gets the list of plaquettes it
+ * belongs to, with the sign it carries there.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int d, periodic, dims[4], nsite, nslot;
+    int *exists;             /* [nslot] */
+    int nplaq;
+    int *plaq_link;          /* [nplaq][4] */
+    int *plaq_sign;          /* [nplaq][4] */
+    int *lp_start;           /* [nslot+1] into lp_plaq/lp_pos */
+    int *lp_plaq, *lp_pos;   /* plaquette index and position of the link in it */
+    int *class_start;        /* [2d+1] */
+    int *class_links;        /* links of class (mu,p) in ascending site order */
+} orc_geom;
+
+static void site_coords(const orc_geom *g, int s, int x[4])
+{
+    for (int i = 0; i < 4; ++i) x[i] = 0;
+    for (int i = 0; i < g->d; ++i) { x[i] = s % g->dims[i]; s /= g->dims[i]; }
+}
+
+static int coords_site(const orc_geom *g, const int x[4])
+{
+    int s = 0;
+    for (int i = g->d - 1; i >= 0; --i) s = s * g->dims[i] + x[i];
+    return s;
+}
+
+/* neighbour of s one step in direction mu (dir = +1 or -1); -1 if it
+ * leaves an open lattice */
+static int neighbour(const orc_geom *g, int s, int mu, int dir)
+{
+    int x[4];
+    site_coords(g, s, x);
+    x[mu] += dir;
+    if (x[mu] < 0 || x[mu] >= g->dims[mu]) {
+        if (!g->periodic) return -1;
+        x[mu] = (x[mu] + g->dims[mu]) % g->dims[mu];
+    }
+    return coords_site(g, x);
+}
+
+orc_geom *orc_geom_new(int d, const int *dims, int periodic)
+{
+    if (d < 1 || d > 4) return NULL;
+    orc_geom *g = (orc_geom *)calloc(1, sizeof(orc_geom));
+    g->d = d; g->periodic = periodic; g->nsite = 1;
+    for (int i = 0; i < d; ++i) { g->dims[i] = dims[i]; g->nsite *= dims[i]; }
+    g->nslot = d * g->nsite;
+    g->exists = (int *)calloc((size_t)g->nslot, sizeof(int));
+    for (int mu = 0; mu < d; ++mu)
+        for (int s = 0; s < g->nsite; ++s)
+            g->exists[mu * g->nsite + s] = neighbour(g, s, mu, +1) >= 0;
+
+    /* plaquettes (x, mu<nu): theta_mu(x) + theta_nu(x+mu) - theta_mu(x+nu) - theta_nu(x) */
+    int maxp = g->nsite * d * (d - 1) / 2;
+    g->plaq_link = (int *)malloc(sizeof(int) * 4 * (size_t)(maxp > 0 ? maxp : 1));
+    g->plaq_sign = (int *)malloc(sizeof(int) * 4 * (size_t)(maxp > 0 ? maxp : 1));
+    g->nplaq = 0;
+    for (int s = 0; s < g->nsite; ++s)
+        for (int mu = 0; mu < d; ++mu)
+            for (int nu = mu + 1; nu < d; ++nu) {
+                int xm = neighbour(g, s, mu, +1), xn = neighbour(g, s, nu, +1);
+                if (xm < 0 || xn < 0) continue;
+                int p = g->nplaq++;
+                g->plaq_link[4 * p + 0] = mu * g->nsite + s;  g->plaq_sign[4 * p + 0] = +1;
+                g->plaq_link[4 * p + 1] = nu * g->nsite + xm; g->plaq_sign[4 * p + 1] = +1;
+                g->plaq_link[4 * p + 2] = mu * g->nsite + xn; g->plaq_sign[4 * p + 2] = -1;
+                g->plaq_link[4 * p + 3] = nu * g->nsite + s;  g->plaq_sign[4 * p + 3] = -1;
+            }
+
+    /* link -> plaquettes */
+    g->lp_start = (int *)calloc((size_t)g->nslot + 1, sizeof(int));
+    for (int p = 0; p < g->nplaq; ++p)
+        for (int j = 0; j < 4; ++j) g->lp_start[g->plaq_link[4 * p + j] + 1]++;
+    for (int l = 0; l < g->nslot; ++l) g->lp_start[l + 1] += g->lp_start[l];
+    int tot = g->lp_start[g->nslot];
+    g->lp_plaq = (int *)malloc(sizeof(int) * (size_t)(tot > 0 ? tot : 1));
+    g->lp_pos = (int *)malloc(sizeof(int) * (size_t)(tot > 0 ? tot : 1));
+    int *fill = (int *)calloc((size_t)g->nslot, sizeof(int));
+    for (int p = 0; p < g->nplaq; ++p)
+        for (int j = 0; j < 4; ++j) {
+            int l = g->plaq_link[4 * p + j];
+            int k = g->lp_start[l] + fill[l]++;
+            g->lp_plaq[k] = p; g->lp_pos[k] = j;
+        }
+    free(fill);
+
+    /* checkerboard classes (mu, parity) in ascending site order */
+    g->class_start = (int *)calloc(2 * (size_t)d + 1, sizeof(int));
+    g->class_links = (int *)malloc(sizeof(int) * (size_t)g->nslot);
+    int n = 0;
+    for (int mu = 0; mu < d; ++mu)
+        for (int par = 0; par < 2; ++par) {
+            g->class_start[2 * mu + par] = n;
+            for (int s = 0; s < g->nsite; ++s) {
+                int x[4]; site_coords(g, s, x);
+                int ps = 0;
+                for (int i = 0; i < d; ++i) ps += x[i];
+                if ((ps & 1) == par && g->exists[mu * g->nsite + s])
+                    g->class_links[n++] = mu * g->nsite + s;
+            }
+        }
+    g->class_start[2 * d] = n;
+    return g;
+}
+
+void orc_geom_free(orc_geom *g)
+{
+    if (!g) return;
+    free(g->exists); free(g->plaq_link); free(g->plaq_sign); free(g->lp_start);
+    free(g->lp_plaq); free(g->lp_pos); free(g->class_start); free(g->class_links);
+    free(g);
+}
+
+int orc_geom_nslot(const orc_geom *g) { return g->nslot; }
+int orc_geom_nplaq(const orc_geom *g) { return g->nplaq; }
+int orc_geom_nsite(const orc_geom *g) { return g->nsite; }
+int orc_geom_link_exists(const orc_geom *g, int l) { return g->exists[l]; }
+
+/* ------------------------------------------------------------------------
+ * Lattice state
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    const orc_geom *g;
+    double *theta;           /* [nslot] */
+    double E;                /* tracked energy */
+    double E_lo, dE;         /* window [E_lo, E_lo + dE] */
+    uint32_t key[2];
+    uint32_t sweep;          /* composite sweeps done (Philox counter word 1) */
+    int n_or, block;
+    double beta_up, beta_dn;
+    /* statistics */
+    double hb_acc, hb_tot, or_acc, or_tot, caps;
+    double max_drift;        /* max |tracked - fresh| seen at a resync */
+    /* scratch */
+    double *prop, *dEl;
+} orc_lat;
+
+#define TAG_HB 0u
+#define TAG_APPROACH 14u
+#define TAG_INIT 15u
+#define SAMPLER_MAX_ATTEMPTS 64
+#define KAPPA_MIN 1e-6
+
+orc_lat *orc_lat_new(const orc_geom *g, uint64_t seed, int interval_id, int replica_id,
+                     double E_lo, double dE, int n_or, int block,
+                     double beta_up, double beta_dn)
+{
+    orc_lat *t = (orc_lat *)calloc(1, sizeof(orc_lat));
+    t->g = g;
+    t->theta = (double *)calloc((size_t)g->nslot, sizeof(double));
+    t->prop = (double *)calloc((size_t)g->nslot, sizeof(double));
+    t->dEl = (double *)calloc((size_t)g->nslot, sizeof(double));
+    t->E_lo = E_lo; t->dE = dE;
+    t->key[0] = (uint32_t)seed ^ (uint32_t)interval_id;
+    t->key[1] = (uint32_t)(seed >> 32) ^ (uint32_t)replica_id;
+    t->n_or = n_or; t->block = block > 0 ? block : 1;
+    t->beta_up = beta_up; t->beta_dn = beta_dn;
+    return t;
+}
+
+void orc_lat_free(orc_lat *t)
+{
+    if (!t) return;
+    free(t->theta); free(t->prop); free(t->dEl); free(t);
+}
+
+/* Fresh energy: sum over plaquettes of cos(theta_P) (Sec. 3.1). */
+double orc_energy(const orc_lat *t)
+{
+    const orc_geom *g = t->g;
+    double E = 0.0;
+    for (int p = 0; p < g->nplaq; ++p) {
+        double a = 0.0;
+        for (int j = 0; j < 4; ++j) a += g->plaq_sign[4 * p + j] * t->theta[g->plaq_link[4 * p + j]];
+        E += cos(a);
+    }
+    return E;
+}
+
+/* Staple angles of link l: cos(theta_P) = cos(theta_l + phi_P) for every
+ * plaquette P that contains l.  Returns their number. */
+static int staples(const orc_lat *t, int l, double *phi)
+{
+    const orc_geom *g = t->g;
+    int n = 0;
+    for (int k = g->lp_start[l]; k < g->lp_start[l + 1]; ++k) {
+        int p = g->lp_plaq[k], pos = g->lp_pos[k];
+        double rest = 0.0;
+        for (int j = 0; j < 4; ++j)
+            if (j != pos) rest += g->plaq_sign[4 * p + j] * t->theta[g->plaq_link[4 * p + j]];
+        phi[n++] = g->plaq_sign[4 * p + pos] * rest;
+    }
+    return n;
+}
+
+/* local energy of link l at angle th: sum_P cos(th + phi_P) */
+static double local_energy(int n, const double *phi, double th)
+{
+    double e = 0.0;
+    for (int j = 0; j < n; ++j) e += cos(th + phi[j]);
+    return e;
+}
+
+void orc_lat_set_links(orc_lat *t, const double *th)
+{
+    memcpy(t->theta, th, sizeof(double) * (size_t)t->g->nslot);
+    t->E = orc_energy(t);
+}
+void orc_lat_get_links(const orc_lat *t, double *th)
+{
+    memcpy(th, t->theta, sizeof(double) * (size_t)t->g->nslot);
+}
+double orc_lat_get_E(const orc_lat *t) { return t->E; }
+void orc_lat_set_E(orc_lat *t, double E) { t->E = E; }
+uint32_t orc_lat_get_sweep(const orc_lat *t) { return t->sweep; }
+void orc_lat_set_sweep(orc_lat *t, uint32_t s) { t->sweep = s; }
+void orc_lat_set_window(orc_lat *t, double E_lo, double dE) { t->E_lo = E_lo; t->dE = dE; }
+void orc_lat_stats(const orc_lat *t, double out[6])
+{
+    out[0] = t->hb_acc; out[1] = t->hb_tot; out[2] = t->or_acc; out[3] = t->or_tot;
+    out[4] = t->caps; out[5] = t->max_drift;
+}
+
+/* Hot start: theta = -pi + 2 pi u, Haar measure (Sec. 3.1). */
+void orc_lat_hot_start(orc_lat *t)
+{
+    const orc_geom *g = t->g;
+    for (int l = 0; l < g->nslot; ++l) {
+        t->theta[l] = 0.0;
+        if (!g->exists[l]) continue;
+        uint32_t ctr[4] = {(uint32_t)l, 0u, TAG_INIT, 0u}, w[4];
+        orc_philox4x32_10(ctr, t->key, w);
+        t->theta[l] = -M_PI + 2.0 * M_PI * orc_uniform(w[0]);
+    }
+    t->E = orc_energy(t);
+}
+
+/* Best & Fisher (1979) von Mises sampler for density ~ exp(kappa cos X).
+ * Returns the number of attempts used, or -1 if the attempt cap was hit. */
+int orc_vonmises(double kappa, const uint32_t key[2], uint32_t c0, uint32_t c1, uint32_t c2,
+                 double *X)
+{
+    if (fabs(kappa) < KAPPA_MIN) {
+        uint32_t ctr[4] = {c0, c1, c2, 0u}, w[4];
+        orc_philox4x32_10(ctr, key, w);
+        *X = M_PI * (2.0 * orc_uniform(w[0]) - 1.0);
+        return 1;
+    }
+    double k = fabs(kappa);
+    double tau = 1.0 + sqrt(1.0 + 4.0 * k * k);
+    double rho = (tau - sqrt(2.0 * tau)) / (2.0 * k);
+    double r = (1.0 + rho * rho) / (2.0 * rho);
+    for (uint32_t att = 0; att < SAMPLER_MAX_ATTEMPTS; ++att) {
+        uint32_t ctr[4] = {c0, c1, c2, att}, w[4];
+        orc_philox4x32_10(ctr, key, w);
+        double u1 = orc_uniform(w[0]), u2 = orc_uniform(w[1]), u3 = orc_uniform(w[2]);
+        double z = cos(M_PI * u1);
+        double f = (1.0 + r * z) / (r + z);
+        double c = k * (r - f);
+        if (c * (2.0 - c) - u2 > 0.0 || log(c / u2) + 1.0 - c >= 0.0) {
+            double x = (u3 > 0.5 ? 1.0 : -1.0) * acos(f);
+            if (kappa < 0.0) x = wrap_angle(x + M_PI);
+            *X = x;
+            return (int)att + 1;
+        }
+    }
+    return -1;
+}
+
+static double dist_to_window(double E, double lo, double hi)
+{
+    if (E < lo) return lo - E;
+    if (E > hi) return E - hi;
+    return 0.0;
+}
+
+/* Update one checkerboard class.  mode 0: heat-bath at parameter a with
+ * Philox tag `tag`; mode 1: overrelaxation. */
+static void class_pass(orc_lat *t, int cls, int mode, double a, uint32_t tag)
+{
+    const orc_geom *g = t->g;
+    double phi[8];
+    double lo = t->E_lo, hi = t->E_lo + t->dE;
+    int c0 = g->class_start[cls], c1 = g->class_start[cls + 1];
+    /* proposals: independent for all links of the class */
+    for (int i = c0; i < c1; ++i) {
+        int l = g->class_links[i];
+        int n = staples(t, l, phi);
+        double Sr = 0.0, Si = 0.0;
+        for (int j = 0; j < n; ++j) { Sr += cos(phi[j]); Si += sin(phi[j]); }
+        double alpha = atan2(Si, Sr), Sabs = sqrt(Sr * Sr + Si * Si);
+        double th = t->theta[l], thn;
+        if (mode == 0) {
+            double X;
+            int att = orc_vonmises(-a * Sabs, t->key, (uint32_t)l, t->sweep, tag, &X);
+            if (att < 0) { thn = th; t->caps += 1.0; }
+            else thn = wrap_angle(X - alpha);
+        } else {
+            thn = wrap_angle(-th - 2.0 * alpha);
+        }
+        t->prop[l] = thn;
+        t->dEl[l] = local_energy(n, phi, thn) - local_energy(n, phi, th);
+    }
+    /* sequential Metropolis accept in blocks of B links, ascending order */
+    for (int b0 = c0; b0 < c1; b0 += t->block) {
+        int b1 = b0 + t->block < c1 ? b0 + t->block : c1;
+        double d = 0.0;
+        for (int i = b0; i < b1; ++i) d += t->dEl[g->class_links[i]];
+        int acc = dist_to_window(t->E + d, lo, hi) <= dist_to_window(t->E, lo, hi);
+        if (acc) {
+            for (int i = b0; i < b1; ++i) t->theta[g->class_links[i]] = t->prop[g->class_links[i]];
+            t->E += d;
+        }
+        if (mode == 0) { t->hb_tot += b1 - b0; if (acc) t->hb_acc += b1 - b0; }
+        else           { t->or_tot += b1 - b0; if (acc) t->or_acc += b1 - b0; }
+    }
+}
+
+/* One pass over all classes in the order mu = 0..d-1, parity 0,1. */
+static void pass(orc_lat *t, int mode, double a, uint32_t tag)
+{
+    for (int cls = 0; cls < 2 * t->g->d; ++cls) class_pass(t, cls, mode, a, tag);
+}
+
+/* One composite sweep: heat-bath pass + n_or overrelaxation passes, then
+ * re-synchronise the tracked energy with the fresh plaquette sum. */
+static void composite_sweep(orc_lat *t, double a, uint32_t tag)
+{
+    pass(t, 0, a, tag);
+    for (int k = 0; k < t->n_or; ++k) pass(t, 1, a, tag);
+    double fresh = orc_energy(t);
+    double drift = fabs(fresh - t->E);
+    if (drift > t->max_drift) t->max_drift = drift;
+    t->E = fresh;
+    t->sweep += 1u;
+}
+
+void orc_lat_sweep(orc_lat *t, double a, int n_sweeps)
+{
+    for (int s = 0; s < n_sweeps; ++s) composite_sweep(t, a, TAG_HB);
+}
+
+/* only the heat-bath pass or only an overrelaxation pass (no resync) */
+void orc_lat_pass(orc_lat *t, int mode, double a)
+{
+    pass(t, mode, a, TAG_HB);
+}
+
+/* a single class (cls = 2 mu + parity), no resync */
+void orc_lat_class_pass(orc_lat *t, int cls, int mode, double a)
+{
+    if (cls >= 0 && cls < 2 * t->g->d) class_pass(t, cls, mode, a, TAG_HB);
+}
+
+/* Approach the window from the current state (reading R5).  Returns the
+ * number of composite sweeps used, or -1 if the window was not reached. */
+int orc_lat_approach(orc_lat *t, int max_sweeps)
+{
+    double lo = t->E_lo, hi = t->E_lo + t->dE;
+    int s = 0;
+    while (dist_to_window(t->E, lo, hi) > 0.0) {
+        if (s >= max_sweeps) return -1;
+        double a = t->E < lo ? -t->beta_up : -t->beta_dn;
+        composite_sweep(t, a, TAG_APPROACH);
+        ++s;
+    }
+    return s;
+}
+
+/* One Robbins-Monro iteration (Algorithm 1 inner loop, eq. kk21):
+ * n_therm + n_meas composite sweeps at weight exp(-a E); the mean of
+ * E - E_lo - dE/2 over the last n_meas sweeps gives <<dE>>; then
+ * a <- a + 12 <<dE>> / (dE^2 (rm_index + 1)).  Returns the new a. */
+double orc_lat_rm_step(orc_lat *t, double a, int n_therm, int n_meas, int rm_index,
+                       double *mean_out)
+{
+    double sum = 0.0;
+    for (int j = 0; j < n_therm + n_meas; ++j) {
+        composite_sweep(t, a, TAG_HB);
+        if (j >= n_therm) sum += t->E - t->E_lo - 0.5 * t->dE;
+    }
+    double mean = n_meas > 0 ? sum / n_meas : 0.0;
+    if (mean_out) *mean_out = mean;
+    return a + 12.0 * mean / (t->dE * t->dE * (double)(rm_index + 1));
+}
+
+/* Per-link staple modulus |S| and angle alpha (for invariance checks). */
+void orc_lat_staple(const orc_lat *t, int l, double out[2])
+{
+    double phi[8];
+    int n = staples(t, l, phi);
+    double Sr = 0.0, Si = 0.0;
+    for (int j = 0; j < n; ++j) { Sr += cos(phi[j]); Si += sin(phi[j]); }
+    out[0] = sqrt(Sr * Sr + Si * Si);
+    out[1] = atan2(Si, Sr);
+}
+
+/* ------------------------------------------------------------------------
+ * Whole LLR runs over many independent (interval, replica) lattices, each
+ * on its own thread: hot start, approach, then n_rm Robbins-Monro
+ * iterations (Algorithm 1).  Used for CPU timing and statistical tests.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    const orc_geom *g;
+    int n_lat, n_threads, next_index;
+    uint64_t seed;
+    const int *interval_id, *replica_id;
+    const double *E_lo, *dE;
+    double *a;               /* [n_lat] in: a^(0); out: final a */
+    double *a_hist;          /* [n_lat][n_rm] or NULL */
+    int n_or, block, n_therm, n_meas, n_rm, rm_offset, max_approach;
+    double beta_up, beta_dn;
+    int *status;             /* [n_lat] 0 ok, -1 window not reached */
+    double *updates;         /* [n_lat] link updates done */
+} orc_batch;
+
+static void *batch_worker(void *arg)
+{
+    void **pa = (void **)arg;
+    orc_batch *b = (orc_batch *)pa[0];
+    int tid = (int)(intptr_t)pa[1];
+    for (int i = tid; i < b->n_lat; i += b->n_threads) {
+        orc_lat *t = orc_lat_new(b->g, b->seed, b->interval_id[i], b->replica_id[i], b->E_lo[i],
+                                 b->dE[i], b->n_or, b->block, b->beta_up, b->beta_dn);
+        orc_lat_hot_start(t);
+        int used = orc_lat_approach(t, b->max_approach);
+        b->status[i] = used < 0 ? -1 : 0;
+        double a = b->a[i];
+        if (used >= 0)
+            for (int n = 0; n < b->n_rm; ++n) {
+                a = orc_lat_rm_step(t, a, b->n_therm, b->n_meas, n + b->rm_offset, NULL);
+                if (b->a_hist) b->a_hist[(size_t)i * b->n_rm + n] = a;
+            }
+        b->a[i] = a;
+        double per_sweep = 0.0;
+        for (int l = 0; l < b->g->nslot; ++l) per_sweep += b->g->exists[l];
+        b->updates[i] = per_sweep * (1 + b->n_or) * ((double)t->sweep);
+        orc_lat_free(t);
+    }
+    return NULL;
+}
+
+int orc_batch_run(const orc_geom *g, int n_lat, uint64_t seed, const int *interval_id,
+                  const int *replica_id, const double *E_lo, const double *dE, double *a,
+                  double *a_hist, int n_or, int block, int n_therm, int n_meas, int n_rm,
+                  int rm_offset, int max_approach, double beta_up, double beta_dn,
+                  int n_threads, int *status, double *updates)
+{
+    orc_batch b = {g, n_lat, n_threads > 0 ? n_threads : 1, 0, seed, interval_id, replica_id,
+                   E_lo, dE, a, a_hist, n_or, block, n_therm, n_meas, n_rm, rm_offset,
+                   max_approach, beta_up, beta_dn, status, updates};
+    pthread_t th[256];
+    void *args[256][2];
+    int nt = b.n_threads > 256 ? 256 : b.n_threads;
+    b.n_threads = nt;
+    for (int i = 0; i < nt; ++i) {
+        args[i][0] = &b; args[i][1] = (void *)(intptr_t)i;
+        pthread_create(&th[i], NULL, batch_worker, args[i]);
+    }
+    for (int i = 0; i < nt; ++i) pthread_join(th[i], NULL);
+    return 0;
+}
