@@ -1,0 +1,323 @@
+"""Benchmark of the LLR hot path on GB300: window-restricted sweeps plus the
+Robbins-Monro update for the whole batch of (interval, replica) lattices.
+
+Workload: 4-D compact U(1), L=20, 256 intervals over E/6V in [0.62, 0.67]
+x 8 replicas (2048 lattices, 5.2 GB of float32 link angles), dE = 12,
+1 heat-bath : 4 overrelaxation.  One step = one Robbins-Monro iteration of
+every lattice (n_therm + n_meas composite sweeps and the update of a).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "link updates/s"
+SFU_OPS_PER_CLK_SM = 16          # sin/cos special-function throughput per SM per clock
+SINCOS_PER_UPDATE = 8            # 6 staples + old and new link angle
+MUFU_PER_SINCOS = 2              # one sine and one cosine
+BYTES_PER_UPDATE = 8             # algorithmic: read + write one float32 link
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n-therm", type=int, default=2)
+    p.add_argument("--n-meas", type=int, default=8)
+    p.add_argument("--threads", type=int, default=256)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--intervals", type=int, default=256)
+    return p.parse_args()
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = [l.strip().split(",") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(args, rank):
+    from paper_1509_08391_gb300 import workloads
+    w = workloads.l20_critical(n_int=args.intervals)
+    # weak scaling: each rank owns its own interval ids
+    w.interval_id = [i + rank * 100000 for i in w.interval_id]
+    w.n_therm, w.n_meas = args.n_therm, args.n_meas
+    return w
+
+
+def config_dict(args, w, world):
+    return {"workload": w.name, "L": 20, "lattices_per_gpu": w.n_lattices,
+            "intervals": args.intervals, "replicas": 8, "dE": 12.0,
+            "E_over_6V": [0.62, 0.67], "hb_or": "1:%d" % w.n_or,
+            "sweeps_per_step": args.n_therm + args.n_meas, "n_therm": args.n_therm,
+            "n_meas": args.n_meas, "accept_block": w.block,
+            "parallelism": "dp%d (independent lattices, no collective)" % world,
+            "l2": "inputs larger than L2 (5.2 GB of links per GPU)"}
+
+
+def cpu_baseline(w, n_sweeps=1, max_lat=None):
+    """The FP64 oracle on a bounded sample of the same workload (host cores)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    n = min(cores, w.n_lattices) if max_lat is None else max_lat
+    g = oracle.Geom([20] * 4)
+    lats = [oracle.Lattice(g, w.seed, w.interval_id[i], w.replica_id[i], w.E_lo[i], w.dE[i],
+                           n_or=w.n_or, block=w.block, beta_up=w.beta_up, beta_dn=w.beta_dn)
+            for i in range(n)]
+    for t in lats:
+        t.hot_start()
+    oracle.parallel_approach(lats, 200, cores)
+    a = np.full(n, w.a0)
+    t0 = time.perf_counter()
+    oracle.parallel_sweeps(lats, a, n_sweeps, cores)
+    dt = time.perf_counter() - t0
+    upd = n * n_sweeps * (1 + w.n_or) * 4 * 20 ** 4
+    return {"value": upd / dt, "unit": METRIC, "cores": min(cores, n), "kind": "oracle",
+            "sample": "%d L=20 lattices of the workload x %d composite sweep(s) (%.3g link "
+                      "updates, %.1f s), FP64 C, one host thread per lattice"
+                      % (n, n_sweeps, upd, dt)}, lats
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the FP64 oracle, as it stands, on the host cores."""
+    w = workload(args, 0)
+    if rank != 0:
+        print(json.dumps({"impl": "reference", "rank": rank, "skipped": "rank 0 runs the oracle"}),
+              file=sys.stderr)
+        return
+    import oracle
+    cores = os.cpu_count() or 1
+    n = min(cores, w.n_lattices)
+    base, lats = cpu_baseline(w, n_sweeps=1, max_lat=n)
+    a = np.full(n, w.a0)
+    for _ in range(args.warmup):
+        oracle.parallel_sweeps(lats, a, 1, cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.parallel_sweeps(lats, a, 1, cores)
+    dt = time.perf_counter() - t0
+    upd = args.steps * n * (1 + w.n_or) * 4 * 20 ** 4
+    v = upd / dt
+    cfg = config_dict(args, w, 1)
+    cfg["reference_sample"] = "%d lattices x 1 composite sweep per step" % n
+    out = {"metric": METRIC, "value": v, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": cfg, "impl": "reference",
+           "cpu_baseline": {"value": v, "unit": METRIC, "cores": n, "kind": "oracle",
+                            "sample": cfg["reference_sample"]},
+           "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    from paper_1509_08391_gb300 import build as bld
+    bld.build()
+    from paper_1509_08391_gb300 import llr
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = workload(args, rank)
+    stream = torch.cuda.Stream(device=dev)
+    b = llr.Batch.from_workload(w, stream=stream.cuda_stream, max_approach=1000)
+    b.set_kernel_config(args.threads, True)
+    n = w.n_lattices
+    upd_per_step = n * (args.n_therm + args.n_meas) * (1 + w.n_or) * 4 * 20 ** 4
+
+    a_dev = torch.full((n,), w.a0, dtype=torch.float64, device=dev)
+    mean_dev = torch.zeros(n, dtype=torch.float64, device=dev)
+    rm = 0
+
+    def step_dev():
+        nonlocal rm
+        b.rm_step_dev(a_dev, a_dev, args.n_therm, args.n_meas, rm, mean_dev)
+        rm += 1
+
+    for _ in range(args.warmup):
+        step_dev()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step_dev()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per_launch_ms = ms / args.steps
+    value = world * upd_per_step * args.steps / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        a_host = torch.full((n,), w.a0, dtype=torch.float64).pin_memory()
+        m_host = torch.zeros(n, dtype=torch.float64).pin_memory()
+        import ctypes
+        lib = llr.load()
+        a_np = a_host.numpy()
+        m_np = m_host.numpy()
+        ke = max(1, args.steps // 2)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for k in range(ke):
+            code = lib.llr_rm_step(b._h, args.n_therm, args.n_meas, rm,
+                                   a_np.ctypes.data_as(ctypes.c_void_p),
+                                   m_np.ctypes.data_as(ctypes.c_void_p))
+            rm += 1
+            if code != 0:
+                raise RuntimeError(lib.llr_last_error().decode())
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * upd_per_step * ke / dt, "unit": METRIC,
+               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 16 * n,
+               "steps": ke}
+
+    st = b.stats()
+    hb = float(st["hb_acc"].sum() / max(st["hb_tot"].sum(), 1))
+    orr = float(st["or_acc"].sum() / max(st["or_tot"].sum(), 1))
+    drift = float(st["max_drift"].max())
+    status_ok = bool(np.all(b.status() == 0))
+    b.close()
+    if rank != 0:
+        return
+
+    # roofline of the dominant kernel (the batched sweep kernel, one launch per step)
+    upd_per_launch = upd_per_step
+    mhz = clk.get("sm_max_mhz") or 2070.0
+    peak_sfu = SFU_OPS_PER_CLK_SM * 152 * mhz * 1e6 / MUFU_PER_SINCOS / 1e9   # Gsincos/s
+    ach_sfu = SINCOS_PER_UPDATE * upd_per_launch / (per_launch_ms / 1e3) / 1e9
+    hbm_peak = 6802.0
+    try:
+        hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except Exception:
+        pass
+    ach_hbm = BYTES_PER_UPDATE * upd_per_launch / (per_launch_ms / 1e3) / 1e9
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "chain_kernel_traffic.json")))
+        if prof.get("sweeps_per_step") == args.n_therm + args.n_meas and prof.get("valid"):
+            traffic = prof["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    out = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_launch_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64",
+        "data": "synthetic (hot start from Philox, seed %d)" % w.seed,
+        "config": config_dict(args, w, world),
+        "rm_intervals_per_s": world * args.intervals * 8 / (per_launch_ms / 1e3),
+        "acceptance": {"heat_bath": hb, "overrelaxation": orr},
+        "max_tracked_minus_fresh": drift, "status_ok": status_ok,
+        "roofline": {"bound": "alu", "achieved": ach_sfu, "peak": peak_sfu,
+                     "unit": "Gsincos/s (SFU pipe)", "frac": ach_sfu / peak_sfu,
+                     "traffic": traffic,
+                     "peak_source": "16 SFU ops/clk/SM x 152 SMs x %.0f MHz / 2 ops per "
+                                    "sincos (derived)" % mhz},
+        "roofline_hbm": {"bound": "hbm", "achieved": ach_hbm, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": ach_hbm / hbm_peak, "peak_source": "MEASURED_PEAKS.json"},
+        "clocks": clk, "gpu_launches": args.steps,
+        "e2e": e2e,
+    }
+    if not args.no_cpu:
+        try:
+            out["cpu_baseline"], _ = cpu_baseline(w)
+        except Exception as e:  # keep the GPU line even if the host baseline fails
+            out["cpu_baseline"] = {"error": str(e)}
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

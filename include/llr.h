@@ -1,0 +1,184 @@
+/*
+ * llr.h -- C ABI of the GB300 (sm_103a) library for the LLR density-of-states
+ * method applied to 4-D compact U(1) lattice gauge theory.
+ *
+ * Paper: K. Langfeld, B. Lucini, R. Pellegrini, A. Rago, "An efficient
+ * algorithm for numerical computations of continuous densities of states",
+ * arXiv:1509.08391.  Equations are cited by the labels of the paper's source
+ * (eq. kk21 = the under-relaxed Robbins-Monro update of Sec. 2.2).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: 0 on success, a negative LLR_ERR_* code on failure;
+ *     llr_last_error() then gives a message (per calling thread).
+ *   - "host" pointers are read or written only during the call; the caller
+ *     owns them.  "device" pointers are CUDA device memory on the handle's
+ *     device, owned by the caller, accessed in stream order on the handle's
+ *     stream (the call returns before the work finishes).
+ *   - A handle owns all the lattice state it allocates (link angles, per
+ *     lattice energies, windows and counters) until llr_destroy.  Calls on
+ *     one handle are not thread safe; they are ordered on the stream given to
+ *     llr_init_lattice (NULL = the legacy default stream).
+ *   - The slope convention follows eq. kk1a: a = d ln rho / dE, and the
+ *     restricted ensemble has weight exp(-a E) on the closed window
+ *     E_lo <= E <= E_lo + dE (eqs. kk7-kk8).  In the physical range a < 0
+ *     and the canonical coupling is beta = -a.
+ *   - Link angles are float32 in [-pi, pi); E = sum over plaquettes of
+ *     cos(theta_P) (Sec. 3.1, beta factored out).  The canonical host layout
+ *     of a lattice's links is index mu * V + s, with V = L^4 and site
+ *     s = ((x3 L + x2) L + x1) L + x0.
+ */
+#ifndef LLR_H
+#define LLR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LLR_OK 0
+#define LLR_ERR_ARG (-1)      /* invalid argument or configuration           */
+#define LLR_ERR_CUDA (-2)     /* a CUDA runtime call failed                  */
+#define LLR_ERR_WINDOW (-3)   /* the approach phase did not reach the window */
+#define LLR_ERR_TIMEOUT (-4)  /* a bounded device wait ran out               */
+#define LLR_ERR_NUMERIC (-5)  /* NaN or infinity in a, E or an accumulator   */
+
+typedef struct llr_ctx *llr_handle;
+
+/* Configuration of a batch of independent (interval, replica) chains.
+ * All arrays are host arrays of length n_lattices. */
+typedef struct {
+    int n_lattices;
+    const int *L;             /* lattice side, even, 2 <= L <= 64              */
+    const double *E_lo;       /* window lower edge E_k (absolute action)       */
+    const double *dE;         /* window width dE > 0                            */
+    const int *interval_id;   /* Philox key word 0 is seed_lo ^ interval_id     */
+    const int *replica_id;    /* Philox key word 1 is seed_hi ^ replica_id      */
+    uint64_t seed;
+    int n_or;                 /* overrelaxation passes per heat-bath pass (>=0) */
+    int accept_block;         /* B: links per window-accept block, 1..32, 2^k   */
+    double beta_up;           /* approach heat-bath beta while E < E_lo         */
+    double beta_dn;           /* approach heat-bath beta while E > E_lo + dE    */
+    int max_approach;         /* approach sweeps at init; 0 = no approach       */
+} llr_config;
+
+/* Create a handle: allocate the lattices in device memory, hot start every
+ * link uniformly on [-pi, pi) (Haar measure, Sec. 3.1) from Philox, compute
+ * the energies, then (if cfg->max_approach > 0) run llr_approach.
+ * cuda_stream: a cudaStream_t or NULL.  Errors: LLR_ERR_ARG (bad config),
+ * LLR_ERR_CUDA, LLR_ERR_WINDOW (approach failed; the handle is still
+ * returned in *out and must be destroyed). */
+int llr_init_lattice(llr_handle *out, const llr_config *cfg, void *cuda_stream);
+
+/* Drive every lattice that is outside its window into it: composite sweeps
+ * at a = -beta_up (E below the window) or a = -beta_dn (E above), accepting
+ * only moves that do not increase the distance to the window, until E lies
+ * in the window after a sweep (the paper does not describe this step).
+ * sweeps_out: host int[n_lattices] or NULL.  Synchronous.
+ * Errors: LLR_ERR_WINDOW if a lattice is still outside after max_sweeps. */
+int llr_approach(llr_handle h, int max_sweeps, int *sweeps_out);
+
+/* n_sweeps composite sweeps at fixed slopes a (host double[n_lattices]),
+ * each one heat-bath pass plus n_or overrelaxation passes restricted to the
+ * window (Sec. 2.4: the importance-sampling update of Algorithm 1 with the
+ * window imposed after the proposal), followed by a fresh plaquette sum.
+ * If measure != 0, dE_sum_out (host double[n_lattices], nullable) receives
+ * the sum over these sweeps of E - E_lo - dE/2 (eq. kk10).  Synchronous. */
+int llr_sweep(llr_handle h, const double *a, int n_sweeps, int measure, double *dE_sum_out);
+
+/* One pass of a composite sweep for every lattice, without the energy
+ * resync and without advancing the sweep counter: kind 0 = heat-bath at the
+ * slopes a (host double[n_lattices]), kind 1 = overrelaxation (a may be
+ * NULL).  Each selected checkerboard class (bit c of class_mask selects
+ * class c = 2 mu + parity; 0xFF = the whole pass, in class order) draws its
+ * proposals and accepts them in link order with the window rule of
+ * llr_sweep.  Synchronous. */
+int llr_pass(llr_handle h, int kind, const double *a, int class_mask);
+
+/* One Robbins-Monro iteration for every lattice (Algorithm 1, eq. kk21):
+ * n_therm + n_meas composite sweeps at a, <<dE>> = mean over the last n_meas
+ * sweeps of E - E_lo - dE/2, then a <- a + 12 <<dE>> / (dE^2 (rm_index + 1)).
+ * a_inout: host double[n_lattices]; dE_mean_out: host double[n_lattices] or
+ * NULL.  The host buffers are copied to and from the device inside the call.
+ * Synchronous.  Errors: LLR_ERR_NUMERIC if a lattice produced a NaN. */
+int llr_rm_step(llr_handle h, int n_therm, int n_meas, int rm_index, double *a_inout,
+                double *dE_mean_out);
+
+/* The same iteration with device buffers and no synchronisation: a_in and
+ * a_out (may alias) and dE_mean_out (nullable) are device double[n_lattices].
+ * All lattices advance in one launch on the handle's stream, so the call can
+ * be captured in a CUDA graph.  Check llr_status afterwards. */
+int llr_rm_step_dev(llr_handle h, int n_therm, int n_meas, int rm_index, const double *a_in,
+                    double *a_out, double *dE_mean_out);
+
+/* The plain per-interval form of the same iteration, kept as the reference
+ * point of the batched form: lattices are processed one after another with
+ * one kernel launch per pass, per energy resync and per update (no batching,
+ * no graph).  Same arguments and results as llr_rm_step.  Synchronous. */
+int llr_rm_step_plain(llr_handle h, int n_therm, int n_meas, int rm_index, double *a_inout,
+                      double *dE_mean_out);
+
+/* Fresh energies E = sum_P cos(theta_P) of every lattice, accumulated in
+ * FP64 from the float32 angles (Sec. 3.1).  E_out: host double[n_lattices]. */
+int llr_energy(llr_handle h, double *E_out);
+
+/* The tracked energies that the window test uses (after the last resync).
+ * E_out: host double[n_lattices]. */
+int llr_tracked_energy(llr_handle h, double *E_out);
+
+/* Copy one lattice's links to / from a host float[4 L^4] in the canonical
+ * layout (index mu * V + s).  llr_set_links also sets that lattice's tracked
+ * energy to the FP64 plaquette sum of the new angles. */
+int llr_get_links(llr_handle h, int lattice, float *out);
+int llr_set_links(llr_handle h, int lattice, const float *in);
+
+/* Composite-sweep counter of a lattice (Philox counter word 1). */
+int llr_get_sweep_counter(llr_handle h, int lattice, uint32_t *out);
+int llr_set_sweep_counter(llr_handle h, int lattice, uint32_t value);
+
+/* Per-lattice statistics, host double[n_lattices][8]: heat-bath accepted,
+ * heat-bath proposed, overrelaxation accepted, overrelaxation proposed,
+ * sampler attempt caps, max |tracked - fresh| energy at a resync (since the
+ * last reset), composite sweeps done, status (0 or an LLR_ERR_* code).
+ * reset != 0 clears the counters afterwards. */
+int llr_stats(llr_handle h, double *out, int reset);
+
+/* Per-lattice status words (0 = fine); host int[n_lattices]. */
+int llr_status(llr_handle h, int *out);
+
+/* Reconstruction of ln rho at the interval centres by the trapezium rule
+ * (eqs. kk3a, kk3b): ln_rho[0] = 0, ln_rho[k+1] = ln_rho[k] + (c[k+1] - c[k])
+ * (a[k] + a[k+1]) / 2.  centres (ascending), a, ln_rho_out: host double[n].
+ * Computed in FP64 on the device. */
+int llr_reconstruct_lnrho(int n, const double *centres, const double *a, double *ln_rho_out);
+
+/* Action observables from the reconstructed density (eqs. l19, l20) at each
+ * of n_beta couplings: ln Z, <E>, <E^2>, in FP64 log-space on the device.
+ * Centres must be equally spaced (weight = spacing).  All host arrays. */
+int llr_observables(int n, const double *centres, const double *a, int n_beta,
+                    const double *beta, double *lnZ_out, double *E_out, double *E2_out);
+
+/* Location of the specific-heat peak C_V = <E^2> - <E>^2 (Sec. 3.4) in
+ * [beta_lo, beta_hi]: a scan over n_grid couplings, then golden-section
+ * refinement to |interval| < tol, all on the device in FP64.
+ * out: host double[2] = {beta_c, C_V(beta_c)}. */
+int llr_cv_peak(int n, const double *centres, const double *a, double beta_lo, double beta_hi,
+                int n_grid, double tol, double *out);
+
+/* Launch shape of the batched sweep kernel: threads per CTA (128, 256 or
+ * 512; one CTA owns one lattice) and fast_math (1: hardware sine/cosine
+ * approximations for the staples, 0: correctly rounded-class sincosf).
+ * Chosen per lattice size by the autotuner; default 256 threads, fast math. */
+int llr_set_kernel_config(llr_handle h, int threads, int fast_math);
+
+/* Release everything the handle owns. */
+int llr_destroy(llr_handle h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *llr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LLR_H */

@@ -79,8 +79,11 @@ def lib():
                 "orc_lat_approach": (I, [P, I]),
                 "orc_lat_rm_step": (D, [P, D, I, I, I, dp]),
                 "orc_lat_staple": (None, [P, I, dp]),
+                "orc_lat_staple_moduli": (None, [P, dp]),
                 "orc_batch_run": (I, [P, I, U64, ip, ip, dp, dp, dp, dp, I, I, I, I, I, I, I,
                                       D, D, I, ip, dp]),
+                "orc_batch_sweeps": (None, [P, dp, I, I, I]),
+                "orc_batch_approach": (None, [P, ip, I, I, I]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -216,6 +219,11 @@ class Lattice:
         lib().orc_lat_staple(self._h, int(link), _dp(out))
         return out
 
+    def staple_moduli(self):
+        out = np.zeros(self.geom.nslot)
+        lib().orc_lat_staple_moduli(self._h, _dp(out))
+        return out
+
     # dynamics
     def sweep(self, a, n=1):
         lib().orc_lat_sweep(self._h, float(a), int(n))
@@ -254,3 +262,21 @@ def batch_run(geom: Geom, seed, interval_id, replica_id, E_lo, dE, a0, n_or=4, b
                         n_therm, n_meas, n_rm, rm_offset, max_approach, float(beta_up),
                         float(beta_dn), int(n_threads), _ip(status), _dp(upd))
     return dict(a=a, history=hist, status=status, updates=upd)
+
+
+def parallel_sweeps(lattices, a, n_sweeps, n_threads):
+    """n_sweeps composite sweeps on each lattice, lattices spread over host threads."""
+    n = len(lattices)
+    arr = (ctypes.c_void_p * n)(*[t._h for t in lattices])
+    av = np.ascontiguousarray(np.broadcast_to(a, (n,)), dtype=np.float64)
+    lib().orc_batch_sweeps(ctypes.cast(arr, ctypes.c_void_p), _dp(av), n, int(n_sweeps),
+                           int(n_threads))
+
+
+def parallel_approach(lattices, max_sweeps, n_threads):
+    n = len(lattices)
+    arr = (ctypes.c_void_p * n)(*[t._h for t in lattices])
+    st = np.zeros(n, dtype=np.int32)
+    lib().orc_batch_approach(ctypes.cast(arr, ctypes.c_void_p), _ip(st), n, int(max_sweeps),
+                             int(n_threads))
+    return st

@@ -508,6 +508,18 @@ void orc_lat_staple(const orc_lat *t, int l, double out[2])
     out[1] = atan2(Si, Sr);
 }
 
+/* |S| of every link slot (0 where the link does not exist). */
+void orc_lat_staple_moduli(const orc_lat *t, double *out)
+{
+    double st[2];
+    for (int l = 0; l < t->g->nslot; ++l) {
+        out[l] = 0.0;
+        if (!t->g->exists[l]) continue;
+        orc_lat_staple(t, l, st);
+        out[l] = st[0];
+    }
+}
+
 /* ------------------------------------------------------------------------
  * Whole LLR runs over many independent (interval, replica) lattices, each
  * on its own thread: hot start, approach, then n_rm Robbins-Monro
@@ -572,4 +584,62 @@ int orc_batch_run(const orc_geom *g, int n_lat, uint64_t seed, const int *interv
     }
     for (int i = 0; i < nt; ++i) pthread_join(th[i], NULL);
     return 0;
+}
+
+/* Run n_sweeps composite sweeps at slope a[i] on existing lattices, one
+ * host thread per lattice group (CPU timing of the same work). */
+typedef struct {
+    orc_lat **lats;
+    const double *a;
+    int n, n_sweeps, n_threads, tid;
+} orc_sweeps_job;
+
+static void *sweeps_worker(void *arg)
+{
+    orc_sweeps_job *j = (orc_sweeps_job *)arg;
+    for (int i = j->tid; i < j->n; i += j->n_threads) orc_lat_sweep(j->lats[i], j->a[i], j->n_sweeps);
+    return NULL;
+}
+
+void orc_batch_sweeps(orc_lat **lats, const double *a, int n, int n_sweeps, int n_threads)
+{
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    pthread_t th[256];
+    orc_sweeps_job jobs[256];
+    for (int t = 0; t < n_threads; ++t) {
+        jobs[t].lats = lats; jobs[t].a = a; jobs[t].n = n; jobs[t].n_sweeps = n_sweeps;
+        jobs[t].n_threads = n_threads; jobs[t].tid = t;
+        pthread_create(&th[t], NULL, sweeps_worker, &jobs[t]);
+    }
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+}
+
+/* approach on existing lattices in parallel; status[i] = sweeps used or -1 */
+typedef struct {
+    orc_lat **lats;
+    int *status;
+    int n, max_sweeps, n_threads, tid;
+} orc_approach_job;
+
+static void *approach_worker(void *arg)
+{
+    orc_approach_job *j = (orc_approach_job *)arg;
+    for (int i = j->tid; i < j->n; i += j->n_threads)
+        j->status[i] = orc_lat_approach(j->lats[i], j->max_sweeps);
+    return NULL;
+}
+
+void orc_batch_approach(orc_lat **lats, int *status, int n, int max_sweeps, int n_threads)
+{
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 256) n_threads = 256;
+    pthread_t th[256];
+    orc_approach_job jobs[256];
+    for (int t = 0; t < n_threads; ++t) {
+        jobs[t].lats = lats; jobs[t].status = status; jobs[t].n = n;
+        jobs[t].max_sweeps = max_sweeps; jobs[t].n_threads = n_threads; jobs[t].tid = t;
+        pthread_create(&th[t], NULL, approach_worker, &jobs[t]);
+    }
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
 }

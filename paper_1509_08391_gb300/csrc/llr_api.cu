@@ -1,0 +1,537 @@
+// llr_api.cu -- host side of the C ABI declared in include/llr.h: argument
+// checking, device allocation of the lattice batch, stream-ordered launches
+// and host <-> device marshalling.  All arithmetic of the method runs in the
+// kernels of llr_chain.cu and llr_recon.cu.
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/llr.h"
+#include "llr_internal.h"
+
+using llr::LatState;
+
+struct llr_ctx {
+    int n = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    float *d_theta = nullptr;
+    size_t n_floats = 0;
+    LatState *d_lat = nullptr;
+    std::vector<LatState> h_lat;     // host copy of the static fields (geometry, window)
+    double *d_a = nullptr, *d_mean = nullptr;
+    int *d_int = nullptr;
+    float *d_links = nullptr;        // staging for llr_get/set_links
+    size_t links_cap = 0;
+    int max_half = 0;
+    int n_or = 4, block = 1;
+    double beta_up = 1.5, beta_dn = 0.5;
+    int threads = 256;
+    bool fast_math = true;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define LLR_CUDA(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(LLR_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+bool pow2_block(int b)
+{
+    return b >= 1 && b <= 32 && (b & (b - 1)) == 0;
+}
+
+llr::ChainArgs base_args(llr_handle h)
+{
+    llr::ChainArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.lats = h->d_lat;
+    a.theta = h->d_theta;
+    a.n_lat = h->n;
+    a.n_or = h->n_or;
+    a.block = h->block;
+    a.beta_up = h->beta_up;
+    a.beta_dn = h->beta_dn;
+    return a;
+}
+
+int check_handle(llr_handle h)
+{
+    if (!h) return fail(LLR_ERR_ARG, "null handle");
+    return LLR_OK;
+}
+
+int pull_states(llr_handle h, std::vector<LatState> &out)
+{
+    out.resize((size_t)h->n);
+    LLR_CUDA(cudaMemcpyAsync(out.data(), h->d_lat, sizeof(LatState) * (size_t)h->n,
+                             cudaMemcpyDeviceToHost, h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    return LLR_OK;
+}
+
+int ensure_links_buffer(llr_handle h, size_t n)
+{
+    if (h->links_cap >= n) return LLR_OK;
+    if (h->d_links) cudaFree(h->d_links);
+    h->d_links = nullptr;
+    h->links_cap = 0;
+    LLR_CUDA(cudaMalloc(&h->d_links, n * sizeof(float)));
+    h->links_cap = n;
+    return LLR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *llr_last_error(void)
+{
+    return g_err.c_str();
+}
+
+int llr_init_lattice(llr_handle *out, const llr_config *cfg, void *cuda_stream)
+{
+    if (!out || !cfg) return fail(LLR_ERR_ARG, "null argument");
+    *out = nullptr;
+    const int n = cfg->n_lattices;
+    if (n <= 0) return fail(LLR_ERR_ARG, "n_lattices must be positive");
+    if (!cfg->L || !cfg->E_lo || !cfg->dE || !cfg->interval_id || !cfg->replica_id)
+        return fail(LLR_ERR_ARG, "null configuration array");
+    if (cfg->n_or < 0 || cfg->n_or > 64) return fail(LLR_ERR_ARG, "n_or must be in [0, 64]");
+    if (!pow2_block(cfg->accept_block))
+        return fail(LLR_ERR_ARG, "accept_block must be a power of two in [1, 32]");
+    if (!std::isfinite(cfg->beta_up) || !std::isfinite(cfg->beta_dn))
+        return fail(LLR_ERR_ARG, "beta_up / beta_dn must be finite");
+    if (cfg->max_approach < 0) return fail(LLR_ERR_ARG, "max_approach must be >= 0");
+
+    std::vector<LatState> st((size_t)n);
+    size_t off = 0;
+    int max_half = 0;
+    for (int i = 0; i < n; ++i) {
+        const int L = cfg->L[i];
+        if (L < 2 || L > 64 || (L & 1))
+            return fail(LLR_ERR_ARG, "lattice " + std::to_string(i) + ": L must be even, 2..64");
+        const double lo = cfg->E_lo[i], w = cfg->dE[i];
+        if (!std::isfinite(lo) || !std::isfinite(w) || !(w > 0.0))
+            return fail(LLR_ERR_ARG, "lattice " + std::to_string(i) + ": bad window");
+        const double hi = lo + w;
+        if (std::fabs(lo) >= 2.0e9 || std::fabs(hi) >= 2.0e9)
+            return fail(LLR_ERR_ARG, "lattice " + std::to_string(i) + ": window beyond +-2e9");
+        LatState &s = st[(size_t)i];
+        std::memset(&s, 0, sizeof(s));
+        const long long V = (long long)L * L * L * L;
+        s.L = L;
+        s.half = (int)(V / 2);
+        s.off = off;
+        off += (size_t)(4 * V);
+        off = (off + 31) & ~(size_t)31;   // 128-byte aligned lattices
+        s.magic = (uint32_t)((4294967296ull + (unsigned long long)L - 1ull) / (unsigned long long)L);
+        s.key0 = (uint32_t)cfg->seed ^ (uint32_t)cfg->interval_id[i];
+        s.key1 = (uint32_t)(cfg->seed >> 32) ^ (uint32_t)cfg->replica_id[i];
+        s.E_lo = lo;
+        s.dE = w;
+        s.lo_fx = (long long)std::ceil(lo * llr::kFx);
+        s.hi_fx = (long long)std::floor(hi * llr::kFx);
+        s.a = -1.0;
+        if (s.half > max_half) max_half = s.half;
+    }
+
+    llr_ctx *h = new llr_ctx();
+    h->n = n;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->n_or = cfg->n_or;
+    h->block = cfg->accept_block;
+    h->beta_up = cfg->beta_up;
+    h->beta_dn = cfg->beta_dn;
+    h->h_lat = st;
+    h->max_half = max_half;
+    h->n_floats = off;
+    cudaGetDevice(&h->device);
+    *out = h;
+
+    LLR_CUDA(cudaMalloc(&h->d_theta, off * sizeof(float)));
+    LLR_CUDA(cudaMalloc(&h->d_lat, sizeof(LatState) * (size_t)n));
+    LLR_CUDA(cudaMalloc(&h->d_a, sizeof(double) * (size_t)n));
+    LLR_CUDA(cudaMalloc(&h->d_mean, sizeof(double) * (size_t)n));
+    LLR_CUDA(cudaMalloc(&h->d_int, sizeof(int) * (size_t)(n + 1)));
+    LLR_CUDA(cudaMemsetAsync(h->d_theta, 0, off * sizeof(float), h->stream));
+    LLR_CUDA(cudaMemcpyAsync(h->d_lat, st.data(), sizeof(LatState) * (size_t)n,
+                             cudaMemcpyHostToDevice, h->stream));
+    LLR_CUDA(llr::launch_hot_start(h->d_lat, h->d_theta, n, max_half, h->stream));
+    llr::ChainArgs a = base_args(h);
+    a.mode = llr::kModeResync;
+    LLR_CUDA(llr::launch_chain(a, h->threads, h->fast_math, h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    if (cfg->max_approach > 0) return llr_approach(h, cfg->max_approach, nullptr);
+    return LLR_OK;
+}
+
+int llr_approach(llr_handle h, int max_sweeps, int *sweeps_out)
+{
+    if (int r = check_handle(h)) return r;
+    if (max_sweeps < 0) return fail(LLR_ERR_ARG, "max_sweeps must be >= 0");
+    llr::ChainArgs a = base_args(h);
+    a.mode = llr::kModeApproach;
+    a.max_approach = max_sweeps;
+    a.approach_sweeps = h->d_int;
+    LLR_CUDA(llr::launch_chain(a, h->threads, h->fast_math, h->stream));
+    if (sweeps_out)
+        LLR_CUDA(cudaMemcpyAsync(sweeps_out, h->d_int, sizeof(int) * (size_t)h->n,
+                                 cudaMemcpyDeviceToHost, h->stream));
+    std::vector<LatState> st;
+    if (int r = pull_states(h, st)) return r;
+    for (int i = 0; i < h->n; ++i)
+        if (st[(size_t)i].status == LLR_ERR_WINDOW)
+            return fail(LLR_ERR_WINDOW, "lattice " + std::to_string(i) +
+                                            " did not reach its window in " +
+                                            std::to_string(max_sweeps) + " sweeps");
+    return LLR_OK;
+}
+
+int llr_sweep(llr_handle h, const double *a_host, int n_sweeps, int measure, double *dE_sum_out)
+{
+    if (int r = check_handle(h)) return r;
+    if (!a_host || n_sweeps < 0) return fail(LLR_ERR_ARG, "bad arguments");
+    LLR_CUDA(cudaMemcpyAsync(h->d_a, a_host, sizeof(double) * (size_t)h->n,
+                             cudaMemcpyHostToDevice, h->stream));
+    llr::ChainArgs a = base_args(h);
+    a.mode = llr::kModeSweeps;
+    a.n_therm = 0;
+    a.n_meas = n_sweeps;
+    a.measure = measure != 0;
+    a.a_in = h->d_a;
+    a.mean_out = h->d_mean;
+    LLR_CUDA(llr::launch_chain(a, h->threads, h->fast_math, h->stream));
+    if (dE_sum_out && measure)
+        LLR_CUDA(cudaMemcpyAsync(dE_sum_out, h->d_mean, sizeof(double) * (size_t)h->n,
+                                 cudaMemcpyDeviceToHost, h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    return LLR_OK;
+}
+
+int llr_pass(llr_handle h, int kind, const double *a_host, int class_mask)
+{
+    if (int r = check_handle(h)) return r;
+    if (kind != 0 && kind != 1) return fail(LLR_ERR_ARG, "kind must be 0 (heat-bath) or 1");
+    if (class_mask < 1 || class_mask > 0xFF) return fail(LLR_ERR_ARG, "class_mask must be in 1..255");
+    if (kind == 0 && !a_host) return fail(LLR_ERR_ARG, "heat-bath pass needs a");
+    llr::ChainArgs a = base_args(h);
+    a.mode = llr::kModePass;
+    a.pass_kind = kind;
+    a.class_mask = class_mask;
+    if (a_host) {
+        LLR_CUDA(cudaMemcpyAsync(h->d_a, a_host, sizeof(double) * (size_t)h->n,
+                                 cudaMemcpyHostToDevice, h->stream));
+        a.a_in = h->d_a;
+    }
+    LLR_CUDA(llr::launch_chain(a, h->threads, h->fast_math, h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    return LLR_OK;
+}
+
+int llr_rm_step_dev(llr_handle h, int n_therm, int n_meas, int rm_index, const double *a_in,
+                    double *a_out, double *dE_mean_out)
+{
+    if (int r = check_handle(h)) return r;
+    if (!a_in || !a_out || n_therm < 0 || n_meas < 1 || rm_index < 0)
+        return fail(LLR_ERR_ARG, "bad arguments");
+    llr::ChainArgs a = base_args(h);
+    a.mode = llr::kModeRM;
+    a.n_therm = n_therm;
+    a.n_meas = n_meas;
+    a.measure = 1;
+    a.rm_index = rm_index;
+    a.a_in = a_in;
+    a.a_out = a_out;
+    a.mean_out = dE_mean_out;
+    LLR_CUDA(llr::launch_chain(a, h->threads, h->fast_math, h->stream));
+    return LLR_OK;
+}
+
+int llr_rm_step(llr_handle h, int n_therm, int n_meas, int rm_index, double *a_inout,
+                double *dE_mean_out)
+{
+    if (int r = check_handle(h)) return r;
+    if (!a_inout) return fail(LLR_ERR_ARG, "null a_inout");
+    LLR_CUDA(cudaMemcpyAsync(h->d_a, a_inout, sizeof(double) * (size_t)h->n,
+                             cudaMemcpyHostToDevice, h->stream));
+    if (int r = llr_rm_step_dev(h, n_therm, n_meas, rm_index, h->d_a, h->d_a, h->d_mean))
+        return r;
+    LLR_CUDA(cudaMemcpyAsync(a_inout, h->d_a, sizeof(double) * (size_t)h->n,
+                             cudaMemcpyDeviceToHost, h->stream));
+    if (dE_mean_out)
+        LLR_CUDA(cudaMemcpyAsync(dE_mean_out, h->d_mean, sizeof(double) * (size_t)h->n,
+                                 cudaMemcpyDeviceToHost, h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < h->n; ++i)
+        if (!std::isfinite(a_inout[i]))
+            return fail(LLR_ERR_NUMERIC, "non-finite a for lattice " + std::to_string(i));
+    return LLR_OK;
+}
+
+int llr_rm_step_plain(llr_handle h, int n_therm, int n_meas, int rm_index, double *a_inout,
+                      double *dE_mean_out)
+{
+    if (int r = check_handle(h)) return r;
+    if (!a_inout || n_therm < 0 || n_meas < 1 || rm_index < 0)
+        return fail(LLR_ERR_ARG, "bad arguments");
+    LLR_CUDA(cudaMemcpyAsync(h->d_a, a_inout, sizeof(double) * (size_t)h->n,
+                             cudaMemcpyHostToDevice, h->stream));
+    llr::ChainArgs a = base_args(h);
+    a.a_in = h->d_a;
+    a.a_out = h->d_a;
+    a.mean_out = h->d_mean;
+    a.rm_index = rm_index;
+    for (int i = 0; i < h->n; ++i) {
+        LLR_CUDA(llr::launch_plain_begin(a, i, h->stream));
+        for (int j = 0; j < n_therm + n_meas; ++j) {
+            LLR_CUDA(llr::launch_plain_pass(a, i, 0, a_inout[i], h->stream));
+            for (int k = 0; k < h->n_or; ++k)
+                LLR_CUDA(llr::launch_plain_pass(a, i, 1, a_inout[i], h->stream));
+            LLR_CUDA(llr::launch_plain_finish(a, i, j >= n_therm, h->stream));
+        }
+        LLR_CUDA(llr::launch_plain_update(a, i, h->stream));
+    }
+    LLR_CUDA(cudaMemcpyAsync(a_inout, h->d_a, sizeof(double) * (size_t)h->n,
+                             cudaMemcpyDeviceToHost, h->stream));
+    if (dE_mean_out)
+        LLR_CUDA(cudaMemcpyAsync(dE_mean_out, h->d_mean, sizeof(double) * (size_t)h->n,
+                                 cudaMemcpyDeviceToHost, h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < h->n; ++i)
+        if (!std::isfinite(a_inout[i]))
+            return fail(LLR_ERR_NUMERIC, "non-finite a for lattice " + std::to_string(i));
+    return LLR_OK;
+}
+
+int llr_energy(llr_handle h, double *E_out)
+{
+    if (int r = check_handle(h)) return r;
+    if (!E_out) return fail(LLR_ERR_ARG, "null E_out");
+    LLR_CUDA(llr::launch_energy_fp64(h->d_lat, h->d_theta, h->n, h->d_mean, h->stream));
+    LLR_CUDA(cudaMemcpyAsync(E_out, h->d_mean, sizeof(double) * (size_t)h->n,
+                             cudaMemcpyDeviceToHost, h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    return LLR_OK;
+}
+
+int llr_tracked_energy(llr_handle h, double *E_out)
+{
+    if (int r = check_handle(h)) return r;
+    if (!E_out) return fail(LLR_ERR_ARG, "null E_out");
+    std::vector<LatState> st;
+    if (int r = pull_states(h, st)) return r;
+    for (int i = 0; i < h->n; ++i) E_out[i] = (double)st[(size_t)i].E_fx * llr::kInvFx;
+    return LLR_OK;
+}
+
+int llr_get_links(llr_handle h, int lattice, float *out)
+{
+    if (int r = check_handle(h)) return r;
+    if (!out || lattice < 0 || lattice >= h->n) return fail(LLR_ERR_ARG, "bad lattice or buffer");
+    const int nl = 8 * h->h_lat[(size_t)lattice].half;
+    if (int r = ensure_links_buffer(h, (size_t)nl)) return r;
+    LLR_CUDA(llr::launch_to_canonical(h->d_lat + lattice, h->d_theta, h->d_links, nl, h->stream));
+    LLR_CUDA(cudaMemcpyAsync(out, h->d_links, sizeof(float) * (size_t)nl, cudaMemcpyDeviceToHost,
+                             h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    return LLR_OK;
+}
+
+int llr_set_links(llr_handle h, int lattice, const float *in)
+{
+    if (int r = check_handle(h)) return r;
+    if (!in || lattice < 0 || lattice >= h->n) return fail(LLR_ERR_ARG, "bad lattice or buffer");
+    const int nl = 8 * h->h_lat[(size_t)lattice].half;
+    if (int r = ensure_links_buffer(h, (size_t)nl)) return r;
+    LLR_CUDA(cudaMemcpyAsync(h->d_links, in, sizeof(float) * (size_t)nl, cudaMemcpyHostToDevice,
+                             h->stream));
+    LLR_CUDA(llr::launch_from_canonical(h->d_lat + lattice, h->d_theta, h->d_links, nl, h->stream));
+    // tracked energy from the FP64 plaquette sum of the new angles
+    LLR_CUDA(llr::launch_energy_fp64(h->d_lat + lattice, h->d_theta, 1, h->d_mean, h->stream));
+    LLR_CUDA(llr::launch_set_energy(h->d_lat + lattice, h->d_mean, h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    return LLR_OK;
+}
+
+int llr_get_sweep_counter(llr_handle h, int lattice, uint32_t *out)
+{
+    if (int r = check_handle(h)) return r;
+    if (!out || lattice < 0 || lattice >= h->n) return fail(LLR_ERR_ARG, "bad lattice");
+    LLR_CUDA(cudaMemcpyAsync(out, (char *)(h->d_lat + lattice) + offsetof(LatState, sweep),
+                             sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    return LLR_OK;
+}
+
+int llr_set_sweep_counter(llr_handle h, int lattice, uint32_t value)
+{
+    if (int r = check_handle(h)) return r;
+    if (lattice < 0 || lattice >= h->n) return fail(LLR_ERR_ARG, "bad lattice");
+    const uint32_t v = value;
+    LLR_CUDA(cudaMemcpyAsync((char *)(h->d_lat + lattice) + offsetof(LatState, sweep), &v,
+                             sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    return LLR_OK;
+}
+
+int llr_stats(llr_handle h, double *out, int reset)
+{
+    if (int r = check_handle(h)) return r;
+    if (!out) return fail(LLR_ERR_ARG, "null out");
+    std::vector<LatState> st;
+    if (int r = pull_states(h, st)) return r;
+    for (int i = 0; i < h->n; ++i) {
+        const LatState &s = st[(size_t)i];
+        double *o = out + 8 * (size_t)i;
+        o[0] = (double)s.hb_acc;
+        o[1] = (double)s.hb_tot;
+        o[2] = (double)s.or_acc;
+        o[3] = (double)s.or_tot;
+        o[4] = (double)s.caps;
+        o[5] = s.max_drift;
+        o[6] = (double)s.sweeps_done;
+        o[7] = (double)s.status;
+    }
+    if (reset) {
+        for (auto &s : st) {
+            s.hb_acc = s.hb_tot = s.or_acc = s.or_tot = s.caps = 0ull;
+            s.max_drift = 0.0;
+            s.sweeps_done = 0ull;
+        }
+        LLR_CUDA(cudaMemcpyAsync(h->d_lat, st.data(), sizeof(LatState) * (size_t)h->n,
+                                 cudaMemcpyHostToDevice, h->stream));
+        LLR_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    return LLR_OK;
+}
+
+int llr_status(llr_handle h, int *out)
+{
+    if (int r = check_handle(h)) return r;
+    if (!out) return fail(LLR_ERR_ARG, "null out");
+    std::vector<LatState> st;
+    if (int r = pull_states(h, st)) return r;
+    for (int i = 0; i < h->n; ++i) out[i] = st[(size_t)i].status;
+    return LLR_OK;
+}
+
+int llr_set_kernel_config(llr_handle h, int threads, int fast_math)
+{
+    if (int r = check_handle(h)) return r;
+    if (threads != 128 && threads != 256 && threads != 512)
+        return fail(LLR_ERR_ARG, "threads must be 128, 256 or 512");
+    h->threads = threads;
+    h->fast_math = fast_math != 0;
+    return LLR_OK;
+}
+
+int llr_destroy(llr_handle h)
+{
+    if (!h) return LLR_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(h->d_theta);
+    cudaFree(h->d_lat);
+    cudaFree(h->d_a);
+    cudaFree(h->d_mean);
+    cudaFree(h->d_int);
+    cudaFree(h->d_links);
+    delete h;
+    return LLR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Reconstruction (stateless; default stream, synchronous)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf()
+    {
+        if (p) cudaFree(p);
+    }
+};
+
+int check_centres(int n, const double *c, const double *a)
+{
+    if (n < 1 || !c || !a) return fail(LLR_ERR_ARG, "need n >= 1 centres and slopes");
+    for (int k = 0; k < n; ++k) {
+        if (!std::isfinite(c[k]) || !std::isfinite(a[k]))
+            return fail(LLR_ERR_ARG, "non-finite centre or slope");
+        if (k > 0 && !(c[k] > c[k - 1])) return fail(LLR_ERR_ARG, "centres must ascend");
+    }
+    return LLR_OK;
+}
+
+}  // namespace
+
+int llr_reconstruct_lnrho(int n, const double *centres, const double *a, double *ln_rho_out)
+{
+    if (int r = check_centres(n, centres, a)) return r;
+    if (!ln_rho_out) return fail(LLR_ERR_ARG, "null output");
+    DevBuf b;
+    LLR_CUDA(cudaMalloc(&b.p, sizeof(double) * 3 * (size_t)n));
+    double *dc = (double *)b.p, *da = dc + n, *dl = da + n;
+    LLR_CUDA(cudaMemcpy(dc, centres, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice));
+    LLR_CUDA(cudaMemcpy(da, a, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice));
+    LLR_CUDA(llr::launch_lnrho(n, dc, da, dl, nullptr));
+    LLR_CUDA(cudaMemcpy(ln_rho_out, dl, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost));
+    return LLR_OK;
+}
+
+int llr_observables(int n, const double *centres, const double *a, int n_beta,
+                    const double *beta, double *lnZ_out, double *E_out, double *E2_out)
+{
+    if (int r = check_centres(n, centres, a)) return r;
+    if (n_beta < 1 || !beta || !lnZ_out || !E_out || !E2_out)
+        return fail(LLR_ERR_ARG, "bad beta arrays");
+    DevBuf b;
+    LLR_CUDA(cudaMalloc(&b.p, sizeof(double) * (3 * (size_t)n + 4 * (size_t)n_beta)));
+    double *dc = (double *)b.p, *da = dc + n, *dl = da + n, *db = dl + n, *dz = db + n_beta,
+           *d1 = dz + n_beta, *d2 = d1 + n_beta;
+    LLR_CUDA(cudaMemcpy(dc, centres, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice));
+    LLR_CUDA(cudaMemcpy(da, a, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice));
+    LLR_CUDA(cudaMemcpy(db, beta, sizeof(double) * (size_t)n_beta, cudaMemcpyHostToDevice));
+    LLR_CUDA(llr::launch_lnrho(n, dc, da, dl, nullptr));
+    LLR_CUDA(llr::launch_observables(n, dc, dl, n_beta, db, dz, d1, d2, nullptr));
+    LLR_CUDA(cudaMemcpy(lnZ_out, dz, sizeof(double) * (size_t)n_beta, cudaMemcpyDeviceToHost));
+    LLR_CUDA(cudaMemcpy(E_out, d1, sizeof(double) * (size_t)n_beta, cudaMemcpyDeviceToHost));
+    LLR_CUDA(cudaMemcpy(E2_out, d2, sizeof(double) * (size_t)n_beta, cudaMemcpyDeviceToHost));
+    return LLR_OK;
+}
+
+int llr_cv_peak(int n, const double *centres, const double *a, double beta_lo, double beta_hi,
+                int n_grid, double tol, double *out)
+{
+    if (int r = check_centres(n, centres, a)) return r;
+    if (!out || n_grid < 2 || !(beta_hi > beta_lo) || !(tol > 0.0))
+        return fail(LLR_ERR_ARG, "bad peak-search arguments");
+    DevBuf b;
+    LLR_CUDA(cudaMalloc(&b.p, sizeof(double) * (3 * (size_t)n + 2)));
+    double *dc = (double *)b.p, *da = dc + n, *dl = da + n, *dout = dl + n;
+    LLR_CUDA(cudaMemcpy(dc, centres, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice));
+    LLR_CUDA(cudaMemcpy(da, a, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice));
+    LLR_CUDA(llr::launch_lnrho(n, dc, da, dl, nullptr));
+    LLR_CUDA(llr::launch_cv_peak(n, dc, dl, beta_lo, beta_hi, n_grid, tol, dout, nullptr));
+    LLR_CUDA(cudaMemcpy(out, dout, sizeof(double) * 2, cudaMemcpyDeviceToHost));
+    return LLR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,189 @@
+// llr_recon.cu -- FP64 reconstruction of ln rho and of action observables
+// from the Robbins-Monro slopes a_k.
+//
+// Paper: Langfeld, Lucini, Pellegrini, Rago (arXiv:1509.08391).
+//   eqs. kk3a, kk3b  ln rho(c_{k+1}) - ln rho(c_k) = (c_{k+1} - c_k) (a_k + a_{k+1}) / 2
+//   eqs. l19, l20    Z(beta) = sum_k w rho(c_k) e^{beta c_k},
+//                    <E^m> = sum_k w c_k^m rho(c_k) e^{beta c_k} / Z
+//   Sec. 3.4         C_V = <E^2> - <E>^2, beta_c at its maximum
+//
+// Sizes are small (hundreds to thousands of intervals), so each quantity is
+// one CTA: a block-wide FP64 scan for ln rho, log-sum-exp reductions for the
+// observables, and a device-side grid scan + golden-section search for the
+// C_V peak.
+#include "llr_internal.h"
+
+namespace llr {
+namespace {
+
+constexpr int kT = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ double block_sum(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < kT / 32; ++w) t += red[w];
+    return t;
+}
+
+__device__ double block_max(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(kFull, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = red[0];
+    for (int w = 1; w < kT / 32; ++w) t = fmax(t, red[w]);
+    return t;
+}
+
+// Inclusive block scan of the trapezium increments, chunk by chunk.
+__device__ void lnrho_scan(int n, const double *c, const double *a, double *out)
+{
+    __shared__ double buf[kT];
+    __shared__ double carry;
+    if (threadIdx.x == 0) carry = 0.0;
+    __syncthreads();
+    for (int base = 0; base < n; base += kT) {
+        const int k = base + threadIdx.x;
+        // increment arriving at centre k (0 for k = 0)
+        double inc = 0.0;
+        if (k > 0 && k < n) inc = 0.5 * (c[k] - c[k - 1]) * (a[k - 1] + a[k]);
+        buf[threadIdx.x] = inc;
+        __syncthreads();
+        for (int o = 1; o < kT; o <<= 1) {
+            const double y = threadIdx.x >= o ? buf[threadIdx.x - o] : 0.0;
+            __syncthreads();
+            buf[threadIdx.x] += y;
+            __syncthreads();
+        }
+        if (k < n) out[k] = carry + buf[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 0) carry += buf[kT - 1];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kT) lnrho_kernel(int n, const double *c, const double *a,
+                                                   double *out)
+{
+    lnrho_scan(n, c, a, out);
+}
+
+// (ln Z, <E>, <E^2>) at coupling beta; ln rho given.  Every thread returns them.
+__device__ void moments_at(int n, const double *c, const double *lr, double beta, double *red,
+                           double &lnZ, double &E1, double &E2)
+{
+    double m = -INFINITY;
+    for (int k = threadIdx.x; k < n; k += kT) m = fmax(m, lr[k] + beta * c[k]);
+    m = block_max(m, red);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int k = threadIdx.x; k < n; k += kT) {
+        const double e = exp(lr[k] + beta * c[k] - m);
+        s0 += e;
+        s1 += c[k] * e;
+        s2 += c[k] * c[k] * e;
+    }
+    s0 = block_sum(s0, red);
+    s1 = block_sum(s1, red);
+    s2 = block_sum(s2, red);
+    const double w = n > 1 ? (c[n - 1] - c[0]) / (double)(n - 1) : 1.0;
+    lnZ = m + log(w * s0);
+    E1 = s1 / s0;
+    E2 = s2 / s0;
+}
+
+__global__ void __launch_bounds__(kT) observables_kernel(int n, const double *c,
+                                                         const double *lr, const double *beta,
+                                                         double *lnZ, double *E1, double *E2)
+{
+    __shared__ double red[kT / 32];
+    double z, e1, e2;
+    moments_at(n, c, lr, beta[blockIdx.x], red, z, e1, e2);
+    if (threadIdx.x == 0) {
+        lnZ[blockIdx.x] = z;
+        E1[blockIdx.x] = e1;
+        E2[blockIdx.x] = e2;
+    }
+}
+
+__device__ double cv_at(int n, const double *c, const double *lr, double beta, double *red)
+{
+    double z, e1, e2;
+    moments_at(n, c, lr, beta, red, z, e1, e2);
+    return e2 - e1 * e1;
+}
+
+__global__ void __launch_bounds__(kT) cv_peak_kernel(int n, const double *c, const double *lr,
+                                                     double blo, double bhi, int n_grid,
+                                                     double tol, double *out)
+{
+    __shared__ double red[kT / 32];
+    int best = 0;
+    double best_cv = -INFINITY;
+    for (int i = 0; i < n_grid; ++i) {
+        const double b = n_grid > 1 ? blo + (bhi - blo) * (double)i / (double)(n_grid - 1) : blo;
+        const double v = cv_at(n, c, lr, b, red);
+        if (v > best_cv) {
+            best_cv = v;
+            best = i;
+        }
+    }
+    const double step = n_grid > 1 ? (bhi - blo) / (double)(n_grid - 1) : 0.0;
+    double lo = blo + step * (double)(best > 0 ? best - 1 : 0);
+    double hi = blo + step * (double)(best < n_grid - 1 ? best + 1 : n_grid - 1);
+    const double g = 0.6180339887498949;   // (sqrt 5 - 1) / 2
+    double x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo);
+    double f1 = cv_at(n, c, lr, x1, red), f2 = cv_at(n, c, lr, x2, red);
+    for (int it = 0; it < 200 && hi - lo > tol; ++it) {
+        if (f1 < f2) {
+            lo = x1;
+            x1 = x2;
+            f1 = f2;
+            x2 = lo + g * (hi - lo);
+            f2 = cv_at(n, c, lr, x2, red);
+        } else {
+            hi = x2;
+            x2 = x1;
+            f2 = f1;
+            x1 = hi - g * (hi - lo);
+            f1 = cv_at(n, c, lr, x1, red);
+        }
+    }
+    const double b = 0.5 * (lo + hi);
+    const double v = cv_at(n, c, lr, b, red);
+    if (threadIdx.x == 0) {
+        out[0] = b;
+        out[1] = v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_lnrho(int n, const double *c, const double *a, double *out, cudaStream_t s)
+{
+    lnrho_kernel<<<1, kT, 0, s>>>(n, c, a, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observables(int n, const double *c, const double *lr, int n_beta,
+                               const double *beta, double *lnZ, double *E1, double *E2,
+                               cudaStream_t s)
+{
+    if (n_beta <= 0) return cudaSuccess;
+    observables_kernel<<<n_beta, kT, 0, s>>>(n, c, lr, beta, lnZ, E1, E2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cv_peak(int n, const double *c, const double *lr, double beta_lo,
+                           double beta_hi, int n_grid, double tol, double *out, cudaStream_t s)
+{
+    cv_peak_kernel<<<1, kT, 0, s>>>(n, c, lr, beta_lo, beta_hi, n_grid, tol, out);
+    return cudaGetLastError();
+}
+
+}  // namespace llr

@@ -1,0 +1,56 @@
+"""The C ABI library loads and exports every entry point include/llr.h declares (no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1509_08391_gb300 import build as b
+from paper_1509_08391_gb300 import llr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "llr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(llr_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    b.build()
+    return ctypes.CDLL(b.LIB)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["llr_init_lattice", "llr_sweep", "llr_rm_step", "llr_reconstruct_lnrho"]:
+        assert n in names
+    assert sorted(llr.EXPORTS) == names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+
+
+def test_binding_loads_and_rejects_bad_config_without_gpu():
+    L = llr.load()
+    # argument validation happens before any CUDA call
+    with pytest.raises(llr.LLRError) as e:
+        llr.Batch([5], [0.0], [1.0], [0], [0], 1)
+    assert e.value.code == llr.LLR_ERR_ARG
+    with pytest.raises(llr.LLRError) as e:
+        llr.Batch([4], [0.0], [-1.0], [0], [0], 1)
+    assert e.value.code == llr.LLR_ERR_ARG
+    with pytest.raises(llr.LLRError) as e:
+        llr.Batch([4], [0.0], [1.0], [0], [0], 1, block=3)
+    assert e.value.code == llr.LLR_ERR_ARG
+    assert L.llr_last_error().decode() != ""
+
+
+def test_reconstruction_rejects_unsorted_centres_without_gpu():
+    with pytest.raises(llr.LLRError) as e:
+        llr.reconstruct_lnrho([2.0, 1.0], [0.0, 0.0])
+    assert e.value.code == llr.LLR_ERR_ARG

@@ -1,0 +1,194 @@
+"""GPU path (CUDA library through the C ABI) against the FP64 oracle.
+
+Tolerances: link angles within 2e-5 rad (modulo 2 pi) after a few sweeps from
+an identical state; FP64 energies within 1e-9 relative on identical angles;
+Robbins-Monro slopes within the combined 3 sigma of the replica spreads.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import recon
+from paper_1509_08391_gb300 import llr, workloads
+from tests.gpu_helpers import (TOL_RAD, check_class_updates, first_mismatch_class,
+                               oracle_mirror, wrapped_diff)
+
+pytestmark = pytest.mark.gpu
+
+TOL_E_REL = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1509_08391_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _batch(w, **kw):
+    return llr.Batch.from_workload(w, **kw)
+
+
+def test_hot_start_is_bit_identical_to_oracle():
+    w = workloads.small_l4()
+    with _batch(w, max_approach=0) as b:
+        g = oracle.Geom([4] * 4)
+        for i in range(w.n_lattices):
+            o = oracle.Lattice(g, w.seed, w.interval_id[i], w.replica_id[i], w.E_lo[i], w.dE[i])
+            o.hot_start()
+            assert np.array_equal(b.get_links(i), o.links().astype(np.float32))
+
+
+@pytest.mark.parametrize("L", [4, 6, 8])
+def test_fp64_energy_matches_oracle_on_same_angles(L):
+    w = workloads.Workload("e", [L] * 3, [0.0] * 3, [1.0] * 3, [0, 1, 2], [0, 0, 0], 42)
+    with _batch(w, max_approach=0) as b:
+        b.sweep(np.full(3, -1.0), 2)    # unrestricted-ish: window far away, dist rule
+        E = b.energy()
+        for i in range(3):
+            o = oracle_mirror(b, w, i)
+            assert abs(E[i] - o.energy()) <= TOL_E_REL * max(1.0, abs(E[i]))
+
+
+def test_tracked_energy_close_to_fresh():
+    w = workloads.small_l4()
+    with _batch(w, max_approach=1000) as b:
+        b.sweep(np.full(w.n_lattices, -1.0), 5)
+        trk, fresh = b.tracked_energy(), b.energy()
+        assert np.max(np.abs(trk - fresh)) < 1e-4
+        st = b.stats()
+        assert np.all(st["max_drift"] < 1e-3)
+        assert np.all(st["status"] == 0)
+
+
+@pytest.mark.parametrize("block", [1, 4])
+def test_each_class_update_matches_oracle_link_by_link(block):
+    """One checkerboard class at a time (heat-bath, then overrelaxation) from an
+    identical state: every link within 2e-5 rad plus its FP32 conditioning
+    term, and the same window decisions."""
+    w = workloads.small_l4()
+    w.block = block
+    a = np.linspace(-1.1, -0.9, w.n_lattices)
+    with _batch(w, max_approach=1000) as b:
+        b.sweep(a, 1)
+        worst = check_class_updates(b, w, range(w.n_lattices), a)
+        assert worst < 1e-3
+
+
+def test_heat_bath_trajectory_matches_oracle():
+    """Three heat-bath sweeps (n_or = 0) from one state: identical window
+    decisions and energies; links agree to 2e-5 rad except where float32
+    differences propagated through later classes of the same pass."""
+    w = workloads.small_l4()
+    w.n_or = 0
+    a = np.linspace(-1.1, -0.9, w.n_lattices)
+    with _batch(w, max_approach=1000) as b:
+        mirrors = [oracle_mirror(b, w, i) for i in range(w.n_lattices)]
+        b.stats(reset=True)
+        b.sweep(a, 3)
+        E = b.energy()
+        Et = b.tracked_energy()
+        st = b.stats()
+        for i, o in enumerate(mirrors):
+            hb0 = o.stats()["hb_acc"]
+            o.sweep(a[i], 3)
+            d = np.abs(wrapped_diff(b.get_links(i), o.links()))
+            assert np.mean(d < TOL_RAD) > 0.99 and d.max() < 1e-3, (i, d.max())
+            assert o.stats()["hb_acc"] - hb0 == st["hb_acc"][i]   # identical decisions
+            o2 = oracle_mirror(b, w, i)
+            assert abs(E[i] - o2.energy()) <= TOL_E_REL * abs(E[i])
+            # links differ by up to 1e-3 rad after propagation, so do the energies
+            assert abs(Et[i] - o.E) < 1e-2
+            assert w.E_lo[i] <= o.E <= w.E_lo[i] + w.dE[i]
+
+
+def test_composite_sweeps_conserve_the_oracle_energies():
+    """Full 1 HB + 4 OR sweeps: the links diverge chaotically through the
+    overrelaxation passes, but overrelaxation conserves E and the heat-bath
+    decisions stay identical, so the energies after each sweep agree."""
+    w = workloads.small_l4()
+    a = np.full(w.n_lattices, -1.0)
+    with _batch(w, max_approach=1000) as b:
+        mirrors = [oracle_mirror(b, w, i) for i in range(w.n_lattices)]
+        for _ in range(2):
+            b.sweep(a, 1)
+            E = b.tracked_energy()
+            for i, o in enumerate(mirrors):
+                o.sweep(a[i], 1)
+                assert abs(E[i] - o.E) < 1e-3, (i, E[i], o.E)
+                # continue both from the GPU state: one sweep at a time
+                o.set_links(b.get_links(i).astype(np.float64))
+                o.sweep_counter = b.get_sweep_counter(i)
+
+
+def test_approach_reaches_every_window():
+    w = workloads.small_l4()
+    with _batch(w, max_approach=0) as b:
+        n_gpu = b.approach(1000)
+        E = b.energy()
+        assert np.all(b.status() == 0)
+    g = oracle.Geom([4] * 4)
+    for i in range(w.n_lattices):
+        o = oracle.Lattice(g, w.seed, w.interval_id[i], w.replica_id[i], w.E_lo[i], w.dE[i],
+                           beta_up=w.beta_up, beta_dn=w.beta_dn)
+        o.hot_start()
+        n = o.approach(1000)
+        assert abs(n - n_gpu[i]) <= 2
+        assert w.E_lo[i] - 1e-5 <= E[i] <= w.E_lo[i] + w.dE[i] + 1e-5
+
+
+def test_plain_form_equals_batched_form():
+    w = workloads.subset(workloads.small_l4(), range(3))
+    a0 = np.full(w.n_lattices, -1.0)
+    with _batch(w, max_approach=1000) as b1, _batch(w, max_approach=1000) as b2:
+        a1, m1 = b1.rm_step(a0, 2, 3, 0)
+        a2, m2 = b2.rm_step_plain(a0, 2, 3, 0)
+        assert np.array_equal(a1, a2) and np.array_equal(m1, m2)
+        for i in range(w.n_lattices):
+            assert np.array_equal(b1.get_links(i), b2.get_links(i))
+
+
+def test_robbins_monro_slopes_agree_with_oracle_statistically():
+    """8 intervals x 4 replicas at L=4, 10 RM steps of 10 + 40 sweeps on both sides:
+    the replica means agree within the combined 3 sigma (plus a floor for
+    intervals whose replicas happen to agree closely)."""
+    R = 4
+    w = workloads.small_l4(replicas=R)
+    n_rm, nth, nme = 10, 10, 40
+    a = np.full(w.n_lattices, w.a0)
+    with _batch(w, max_approach=1000) as b:
+        for n in range(n_rm):
+            a, _ = b.rm_step(a, nth, nme, n)
+        assert np.all(b.status() == 0)
+    g = oracle.Geom([4] * 4)
+    out = oracle.batch_run(g, w.seed, w.interval_id, w.replica_id, w.E_lo, w.dE,
+                           np.full(w.n_lattices, w.a0), n_or=w.n_or, block=w.block, n_therm=nth,
+                           n_meas=nme, n_rm=n_rm, max_approach=1000, beta_up=w.beta_up,
+                           beta_dn=w.beta_dn, n_threads=min(16, os.cpu_count() or 1))
+    ao = out["a"]
+    ga = a.reshape(8, R)
+    oa = ao.reshape(8, R)
+    sig = np.sqrt(ga.var(axis=1, ddof=1) / R + oa.var(axis=1, ddof=1) / R)
+    diff = np.abs(ga.mean(axis=1) - oa.mean(axis=1))
+    assert np.all(diff <= 3 * sig + 0.01), (diff, sig)
+
+
+def test_reconstruction_matches_oracle():
+    rng = np.random.default_rng(0)
+    c = np.linspace(900.0, 1100.0, 257)
+    a = -1.0 + 0.002 * (c - 1000.0) + 0.01 * rng.normal(size=c.size)
+    ln_g = llr.reconstruct_lnrho(c, a)
+    ln_o = recon.lnrho_at_centres(c, a)
+    assert np.max(np.abs(ln_g - ln_o)) < 1e-10 * max(1.0, np.max(np.abs(ln_o)))
+    betas = np.linspace(0.5, 1.5, 11)
+    lz, e1, e2 = llr.observables(c, a, betas)
+    for k, bt in enumerate(betas):
+        z, E1, E2 = recon.moments(c, a, bt)
+        assert abs(lz[k] - z) < 1e-9 * max(1.0, abs(z))
+        assert abs(e1[k] - E1) < 1e-9 * abs(E1)
+        assert abs((e2[k] - e1[k] ** 2) - (E2 - E1 ** 2)) < 1e-6 * max(1.0, E2 - E1 ** 2)
+    bg, cg = llr.cv_peak(c, a, 0.5, 1.5, 2001, 1e-12)
+    bo, co = recon.cv_peak(c, a, 0.5, 1.5, 2001, 1e-12)
+    assert abs(bg - bo) < 1e-8 and abs(cg - co) < 1e-8 * max(1.0, co)
