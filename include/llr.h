@@ -158,6 +158,32 @@ int llr_reconstruct_lnrho(int n, const double *centres, const double *a, double 
 int llr_observables(int n, const double *centres, const double *a, int n_beta,
                     const double *beta, double *lnZ_out, double *E_out, double *E2_out);
 
+/* Largest number of interval centres llr_observables_noalloc accepts. */
+#define LLR_NOALLOC_MAX_CENTRES 65536
+
+/* llr_observables for callers that cannot allocate device memory, such as a
+ * host application that hands out all device memory from its own
+ * preallocated pool, or code that must not call cudaMalloc/cudaFree while it
+ * runs (they synchronise the device).  It computes the same ln Z, <E>, <E^2>
+ * without any allocation: the intermediate ln rho lives in a fixed device
+ * array of LLR_NOALLOC_MAX_CENTRES doubles (512 KiB) that every GPU loading
+ * this library keeps until the process exits.  The paper has no counterpart
+ * of this entry point.
+ *   centres, a: device double[n] (centres equally spaced and ascending: they
+ *     are not checked, they stay on the device); beta: device double[n_beta];
+ *   lnZ_out, E_out, E2_out: device double[n_beta]; cuda_stream: a
+ *     cudaStream_t or NULL.  The call only enqueues work on that stream.
+ *   Errors: LLR_ERR_ARG if n is outside 1..LLR_NOALLOC_MAX_CENTRES or a
+ *     pointer is NULL; LLR_ERR_CUDA if the set-up or a launch fails.
+ * The first call on a device looks up the device address of the array (with
+ * that device current), so make that first call before any stream capture.
+ * Every call reuses the same array and leaves its last contents there; calls
+ * whose work overlaps on the GPU (different streams, or different host
+ * threads on one device) race on it and must be serialised by the caller. */
+int llr_observables_noalloc(int n, const double *centres, const double *a, int n_beta,
+                            const double *beta, double *lnZ_out, double *E_out, double *E2_out,
+                            void *cuda_stream);
+
 /* Location of the specific-heat peak C_V = <E^2> - <E>^2 (Sec. 3.4) in
  * [beta_lo, beta_hi]: a scan over n_grid couplings, then golden-section
  * refinement to |interval| < tol, all on the device in FP64.

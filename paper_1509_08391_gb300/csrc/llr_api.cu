@@ -97,6 +97,11 @@ int ensure_links_buffer(llr_handle h, size_t n)
 
 }  // namespace
 
+int llr::set_last_error(int code, const char *msg)
+{
+    return fail(code, msg);
+}
+
 extern "C" {
 
 const char *llr_last_error(void)

@@ -65,6 +65,9 @@ cudaError_t launch_to_canonical(const LatState *lat_dev, const float *theta, flo
 cudaError_t launch_from_canonical(const LatState *lat_dev, float *theta, const float *in,
                                   int n_links, cudaStream_t s);
 
+// Record the message returned by llr_last_error() on this thread; returns code.
+int set_last_error(int code, const char *msg);
+
 // Reconstruction kernels.
 cudaError_t launch_lnrho(int n, const double *c, const double *a, double *out, cudaStream_t s);
 cudaError_t launch_observables(int n, const double *c, const double *a, int n_beta,

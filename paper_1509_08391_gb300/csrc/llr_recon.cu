@@ -11,7 +11,18 @@
 // one CTA: a block-wide FP64 scan for ln rho, log-sum-exp reductions for the
 // observables, and a device-side grid scan + golden-section search for the
 // C_V peak.
+#include <mutex>
+#include <string>
+
+#include "../../include/llr.h"
 #include "llr_internal.h"
+
+// Scratch of llr_observables_noalloc: ln rho at up to LLR_NOALLOC_MAX_CENTRES
+// interval centres, in a fixed device array that every GPU loading this
+// library holds until the process exits.  Host code must not pass the symbol
+// itself to a kernel (on the host it names a host-side stand-in); it uses the
+// device address that cudaGetSymbolAddress returns.
+static __device__ __align__(256) double g_noalloc_lnrho[LLR_NOALLOC_MAX_CENTRES];
 
 namespace llr {
 namespace {
@@ -187,3 +198,59 @@ cudaError_t launch_cv_peak(int n, const double *c, const double *lr, double beta
 }
 
 }  // namespace llr
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device with that device current.
+int noalloc_scratch(double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return llr::set_last_error(LLR_ERR_CUDA, (std::string("cudaGetDevice: ") +
+                                                  cudaGetErrorString(e)).c_str());
+    if (dev < 0 || dev >= kMaxDevices)
+        return llr::set_last_error(LLR_ERR_ARG, "device ordinal beyond 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_lnrho);
+        if (e != cudaSuccess || !p)
+            return llr::set_last_error(LLR_ERR_CUDA, (std::string("cudaGetSymbolAddress: ") +
+                                                      cudaGetErrorString(e)).c_str());
+        g_noalloc_ptr[dev] = (double *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return LLR_OK;
+}
+
+}  // namespace
+
+extern "C" int llr_observables_noalloc(int n, const double *centres, const double *a,
+                                       int n_beta, const double *beta, double *lnZ_out,
+                                       double *E_out, double *E2_out, void *cuda_stream)
+{
+    if (n < 1 || n > LLR_NOALLOC_MAX_CENTRES)
+        return llr::set_last_error(LLR_ERR_ARG, ("n must be in 1.." +
+                                                 std::to_string(LLR_NOALLOC_MAX_CENTRES) +
+                                                 " for llr_observables_noalloc").c_str());
+    if (n_beta < 1 || !centres || !a || !beta || !lnZ_out || !E_out || !E2_out)
+        return llr::set_last_error(LLR_ERR_ARG, "null device buffer or n_beta < 1");
+    double *scratch = nullptr;
+    if (int r = noalloc_scratch(&scratch)) return r;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // every call writes ln rho at all n centres before the observables read
+    // them, so the scratch needs no clearing between calls
+    cudaError_t e = llr::launch_lnrho(n, centres, a, scratch, s);
+    if (e == cudaSuccess)
+        e = llr::launch_observables(n, centres, scratch, n_beta, beta, lnZ_out, E_out, E2_out, s);
+    if (e != cudaSuccess)
+        return llr::set_last_error(LLR_ERR_CUDA, (std::string("launch: ") +
+                                                  cudaGetErrorString(e)).c_str());
+    return LLR_OK;
+}

@@ -27,8 +27,9 @@ EXPORTS = [
     "llr_rm_step_plain", "llr_energy", "llr_tracked_energy", "llr_get_links", "llr_set_links",
     "llr_get_sweep_counter", "llr_set_sweep_counter", "llr_stats", "llr_status",
     "llr_reconstruct_lnrho", "llr_observables", "llr_cv_peak", "llr_set_kernel_config",
-    "llr_destroy", "llr_last_error",
+    "llr_destroy", "llr_last_error", "llr_observables_noalloc",
 ]
+NOALLOC_MAX_CENTRES = 65536
 
 _lib = None
 
@@ -87,6 +88,7 @@ def load(path: str = LIB_PATH):
         "llr_cv_peak": [I, P, P, D, D, I, D, P],
         "llr_set_kernel_config": [P, I, I],
         "llr_destroy": [P],
+        "llr_observables_noalloc": [I, P, P, I, P, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -270,3 +272,14 @@ def cv_peak(centres, a, beta_lo, beta_hi, n_grid=2001, tol=1e-12):
     _check(load().llr_cv_peak(len(c), _ptr(c), _ptr(a), float(beta_lo), float(beta_hi),
                               int(n_grid), float(tol), _ptr(out)))
     return float(out[0]), float(out[1])
+
+
+def observables_noalloc(centres_dev, a_dev, beta_dev, lnZ_dev, E_dev, E2_dev, stream=None):
+    """llr_observables_noalloc on caller-owned device buffers (torch tensors or
+    raw device pointers); enqueues on `stream` and allocates nothing."""
+    n = centres_dev.numel() if hasattr(centres_dev, "numel") else None
+    nb = beta_dev.numel() if hasattr(beta_dev, "numel") else None
+    _check(load().llr_observables_noalloc(int(n), _dev_ptr(centres_dev), _dev_ptr(a_dev),
+                                          int(nb), _dev_ptr(beta_dev), _dev_ptr(lnZ_dev),
+                                          _dev_ptr(E_dev), _dev_ptr(E2_dev),
+                                          ctypes.c_void_p(stream) if stream else None))
