@@ -143,7 +143,9 @@ int llr_set_sweep_counter(llr_handle h, int lattice, uint32_t value);
  * reset != 0 clears the counters afterwards. */
 int llr_stats(llr_handle h, double *out, int reset);
 
-/* Per-lattice status words (0 = fine); host int[n_lattices]. */
+/* Per-lattice status words (0 = fine); host int[n_lattices].  Returns
+ * LLR_ERR_TIMEOUT if, in the last batched launch, a bounded device wait for a
+ * lattice's previous sweep ran out (that lattice was then left unchanged). */
 int llr_status(llr_handle h, int *out);
 
 /* Reconstruction of ln rho at the interval centres by the trapezium rule

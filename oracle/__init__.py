@@ -76,6 +76,7 @@ def lib():
                 "orc_lat_sweep": (None, [P, D, I]),
                 "orc_lat_pass": (None, [P, I, D]),
                 "orc_lat_class_pass": (None, [P, I, I, D]),
+                "orc_lat_class_trace": (I, [P, I, I, D, dp, dp, dp, dp, ip]),
                 "orc_lat_approach": (I, [P, I]),
                 "orc_lat_rm_step": (D, [P, D, I, I, I, dp]),
                 "orc_lat_staple": (None, [P, I, dp]),
@@ -233,6 +234,17 @@ class Lattice:
 
     def class_pass(self, cls, mode, a=0.0):
         lib().orc_lat_class_pass(self._h, int(cls), int(mode), float(a))
+
+    def class_trace(self, cls, mode, a=0.0):
+        """class_pass plus, per link in update order: old angle, proposal, energy
+        before its block, the block's dE and the accept decision."""
+        n = self.geom.nslot
+        bufs = [np.zeros(n) for _ in range(4)]
+        acc = np.zeros(n, dtype=np.int32)
+        m = lib().orc_lat_class_trace(self._h, int(cls), int(mode), float(a), _dp(bufs[0]),
+                                      _dp(bufs[1]), _dp(bufs[2]), _dp(bufs[3]), _ip(acc))
+        return dict(th_old=bufs[0][:m], th_prop=bufs[1][:m], E_before=bufs[2][:m],
+                    dE=bufs[3][:m], accepted=acc[:m].astype(bool))
 
     def approach(self, max_sweeps):
         return lib().orc_lat_approach(self._h, int(max_sweeps))

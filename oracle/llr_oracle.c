@@ -429,6 +429,37 @@ static void class_pass(orc_lat *t, int cls, int mode, double a, uint32_t tag)
     }
 }
 
+/* The same class update as class_pass, recording for every link of the
+ * class (in update order) its old angle, its proposal, the energy before its
+ * block, the block's dE and whether the block was accepted (test
+ * diagnostics: how close a window decision was to a tie). */
+int orc_lat_class_trace(orc_lat *t, int cls, int mode, double a, double *th_old, double *th_prop,
+                        double *E_before, double *dE_block, int *accepted)
+{
+    const orc_geom *g = t->g;
+    if (cls < 0 || cls >= 2 * g->d) return 0;
+    int c0 = g->class_start[cls], c1 = g->class_start[cls + 1];
+    for (int i = c0; i < c1; ++i) th_old[i - c0] = t->theta[g->class_links[i]];
+    double lo = t->E_lo, hi = t->E_lo + t->dE;
+    /* replay the decisions of class_pass on a copy of the energy */
+    double E = t->E;
+    class_pass(t, cls, mode, a, TAG_HB);
+    for (int b0 = c0; b0 < c1; b0 += t->block) {
+        int b1 = b0 + t->block < c1 ? b0 + t->block : c1;
+        double d = 0.0;
+        for (int i = b0; i < b1; ++i) d += t->dEl[g->class_links[i]];
+        int acc = dist_to_window(E + d, lo, hi) <= dist_to_window(E, lo, hi);
+        for (int i = b0; i < b1; ++i) {
+            th_prop[i - c0] = t->prop[g->class_links[i]];
+            E_before[i - c0] = E;
+            dE_block[i - c0] = d;
+            accepted[i - c0] = acc;
+        }
+        if (acc) E += d;
+    }
+    return c1 - c0;
+}
+
 /* One pass over all classes in the order mu = 0..d-1, parity 0,1. */
 static void pass(orc_lat *t, int mode, double a, uint32_t tag)
 {

@@ -29,8 +29,9 @@ struct llr_ctx {
     int max_half = 0;
     int n_or = 4, block = 1;
     double beta_up = 1.5, beta_dn = 0.5;
-    int threads = 256;
-    bool fast_math = true;
+    llr::LaunchCfg cfg;
+    unsigned *d_sync = nullptr;      // work queue of the persistent kernel: 2 + n words
+    int *d_order = nullptr;          // 0 .. n-1 (single-lattice launches point into it)
 };
 
 namespace {
@@ -55,9 +56,12 @@ bool pow2_block(int b)
     return b >= 1 && b <= 32 && (b & (b - 1)) == 0;
 }
 
-llr::ChainArgs base_args(llr_handle h)
+// A lattice's previous sweep is never waited for longer than this.
+constexpr unsigned long long kWaitLimitNs = 20000000000ull;
+
+llr::KernelArgs base_args(llr_handle h)
 {
-    llr::ChainArgs a;
+    llr::KernelArgs a;
     std::memset(&a, 0, sizeof(a));
     a.lats = h->d_lat;
     a.theta = h->d_theta;
@@ -66,7 +70,21 @@ llr::ChainArgs base_args(llr_handle h)
     a.block = h->block;
     a.beta_up = h->beta_up;
     a.beta_dn = h->beta_dn;
+    a.class_mask = 0xFF;
+    a.sync = h->d_sync;
+    a.wait_limit_ns = kWaitLimitNs;
     return a;
+}
+
+// Error word of the last persistent launch (nonzero: a bounded wait ran out).
+int check_queue(llr_handle h)
+{
+    unsigned w = 0;
+    LLR_CUDA(cudaMemcpyAsync(&w, h->d_sync + 1, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                             h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    if (w) return fail(LLR_ERR_TIMEOUT, "a lattice's previous sweep was not done in time");
+    return LLR_OK;
 }
 
 int check_handle(llr_handle h)
@@ -174,13 +192,21 @@ int llr_init_lattice(llr_handle *out, const llr_config *cfg, void *cuda_stream)
     LLR_CUDA(cudaMalloc(&h->d_a, sizeof(double) * (size_t)n));
     LLR_CUDA(cudaMalloc(&h->d_mean, sizeof(double) * (size_t)n));
     LLR_CUDA(cudaMalloc(&h->d_int, sizeof(int) * (size_t)(n + 1)));
+    LLR_CUDA(cudaMalloc(&h->d_sync, sizeof(unsigned) * (size_t)(n + 2)));
+    LLR_CUDA(cudaMalloc(&h->d_order, sizeof(int) * (size_t)n));
+    {
+        std::vector<int> ord((size_t)n);
+        for (int i = 0; i < n; ++i) ord[(size_t)i] = i;
+        LLR_CUDA(cudaMemcpy(h->d_order, ord.data(), sizeof(int) * (size_t)n,
+                            cudaMemcpyHostToDevice));
+    }
     LLR_CUDA(cudaMemsetAsync(h->d_theta, 0, off * sizeof(float), h->stream));
     LLR_CUDA(cudaMemcpyAsync(h->d_lat, st.data(), sizeof(LatState) * (size_t)n,
                              cudaMemcpyHostToDevice, h->stream));
     LLR_CUDA(llr::launch_hot_start(h->d_lat, h->d_theta, n, max_half, h->stream));
-    llr::ChainArgs a = base_args(h);
-    a.mode = llr::kModeResync;
-    LLR_CUDA(llr::launch_chain(a, h->threads, h->fast_math, h->stream));
+    llr::KernelArgs a = base_args(h);
+    a.program = llr::kProgResync;
+    LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
     LLR_CUDA(cudaStreamSynchronize(h->stream));
     if (cfg->max_approach > 0) return llr_approach(h, cfg->max_approach, nullptr);
     return LLR_OK;
@@ -190,11 +216,11 @@ int llr_approach(llr_handle h, int max_sweeps, int *sweeps_out)
 {
     if (int r = check_handle(h)) return r;
     if (max_sweeps < 0) return fail(LLR_ERR_ARG, "max_sweeps must be >= 0");
-    llr::ChainArgs a = base_args(h);
-    a.mode = llr::kModeApproach;
+    llr::KernelArgs a = base_args(h);
+    a.program = llr::kProgApproach;
     a.max_approach = max_sweeps;
     a.approach_sweeps = h->d_int;
-    LLR_CUDA(llr::launch_chain(a, h->threads, h->fast_math, h->stream));
+    LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
     if (sweeps_out)
         LLR_CUDA(cudaMemcpyAsync(sweeps_out, h->d_int, sizeof(int) * (size_t)h->n,
                                  cudaMemcpyDeviceToHost, h->stream));
@@ -214,19 +240,19 @@ int llr_sweep(llr_handle h, const double *a_host, int n_sweeps, int measure, dou
     if (!a_host || n_sweeps < 0) return fail(LLR_ERR_ARG, "bad arguments");
     LLR_CUDA(cudaMemcpyAsync(h->d_a, a_host, sizeof(double) * (size_t)h->n,
                              cudaMemcpyHostToDevice, h->stream));
-    llr::ChainArgs a = base_args(h);
-    a.mode = llr::kModeSweeps;
+    llr::KernelArgs a = base_args(h);
+    a.program = llr::kProgSweeps;
     a.n_therm = 0;
     a.n_meas = n_sweeps;
     a.measure = measure != 0;
     a.a_in = h->d_a;
     a.mean_out = h->d_mean;
-    LLR_CUDA(llr::launch_chain(a, h->threads, h->fast_math, h->stream));
+    LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
     if (dE_sum_out && measure)
         LLR_CUDA(cudaMemcpyAsync(dE_sum_out, h->d_mean, sizeof(double) * (size_t)h->n,
                                  cudaMemcpyDeviceToHost, h->stream));
     LLR_CUDA(cudaStreamSynchronize(h->stream));
-    return LLR_OK;
+    return check_queue(h);
 }
 
 int llr_pass(llr_handle h, int kind, const double *a_host, int class_mask)
@@ -235,8 +261,8 @@ int llr_pass(llr_handle h, int kind, const double *a_host, int class_mask)
     if (kind != 0 && kind != 1) return fail(LLR_ERR_ARG, "kind must be 0 (heat-bath) or 1");
     if (class_mask < 1 || class_mask > 0xFF) return fail(LLR_ERR_ARG, "class_mask must be in 1..255");
     if (kind == 0 && !a_host) return fail(LLR_ERR_ARG, "heat-bath pass needs a");
-    llr::ChainArgs a = base_args(h);
-    a.mode = llr::kModePass;
+    llr::KernelArgs a = base_args(h);
+    a.program = llr::kProgPass;
     a.pass_kind = kind;
     a.class_mask = class_mask;
     if (a_host) {
@@ -244,9 +270,9 @@ int llr_pass(llr_handle h, int kind, const double *a_host, int class_mask)
                                  cudaMemcpyHostToDevice, h->stream));
         a.a_in = h->d_a;
     }
-    LLR_CUDA(llr::launch_chain(a, h->threads, h->fast_math, h->stream));
+    LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
     LLR_CUDA(cudaStreamSynchronize(h->stream));
-    return LLR_OK;
+    return check_queue(h);
 }
 
 int llr_rm_step_dev(llr_handle h, int n_therm, int n_meas, int rm_index, const double *a_in,
@@ -255,8 +281,8 @@ int llr_rm_step_dev(llr_handle h, int n_therm, int n_meas, int rm_index, const d
     if (int r = check_handle(h)) return r;
     if (!a_in || !a_out || n_therm < 0 || n_meas < 1 || rm_index < 0)
         return fail(LLR_ERR_ARG, "bad arguments");
-    llr::ChainArgs a = base_args(h);
-    a.mode = llr::kModeRM;
+    llr::KernelArgs a = base_args(h);
+    a.program = llr::kProgRM;
     a.n_therm = n_therm;
     a.n_meas = n_meas;
     a.measure = 1;
@@ -264,7 +290,7 @@ int llr_rm_step_dev(llr_handle h, int n_therm, int n_meas, int rm_index, const d
     a.a_in = a_in;
     a.a_out = a_out;
     a.mean_out = dE_mean_out;
-    LLR_CUDA(llr::launch_chain(a, h->threads, h->fast_math, h->stream));
+    LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
     return LLR_OK;
 }
 
@@ -283,6 +309,7 @@ int llr_rm_step(llr_handle h, int n_therm, int n_meas, int rm_index, double *a_i
         LLR_CUDA(cudaMemcpyAsync(dE_mean_out, h->d_mean, sizeof(double) * (size_t)h->n,
                                  cudaMemcpyDeviceToHost, h->stream));
     LLR_CUDA(cudaStreamSynchronize(h->stream));
+    if (int r = check_queue(h)) return r;
     for (int i = 0; i < h->n; ++i)
         if (!std::isfinite(a_inout[i]))
             return fail(LLR_ERR_NUMERIC, "non-finite a for lattice " + std::to_string(i));
@@ -297,20 +324,29 @@ int llr_rm_step_plain(llr_handle h, int n_therm, int n_meas, int rm_index, doubl
         return fail(LLR_ERR_ARG, "bad arguments");
     LLR_CUDA(cudaMemcpyAsync(h->d_a, a_inout, sizeof(double) * (size_t)h->n,
                              cudaMemcpyHostToDevice, h->stream));
-    llr::ChainArgs a = base_args(h);
+    // one lattice at a time, one launch of the same kernel per pass, resync, update
+    llr::KernelArgs a = base_args(h);
+    a.n_lat = 1;
     a.a_in = h->d_a;
     a.a_out = h->d_a;
     a.mean_out = h->d_mean;
     a.rm_index = rm_index;
     for (int i = 0; i < h->n; ++i) {
-        LLR_CUDA(llr::launch_plain_begin(a, i, h->stream));
+        a.order = h->d_order + i;
+        a.program = llr::kProgBegin;
+        LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
         for (int j = 0; j < n_therm + n_meas; ++j) {
-            LLR_CUDA(llr::launch_plain_pass(a, i, 0, a_inout[i], h->stream));
-            for (int k = 0; k < h->n_or; ++k)
-                LLR_CUDA(llr::launch_plain_pass(a, i, 1, a_inout[i], h->stream));
-            LLR_CUDA(llr::launch_plain_finish(a, i, j >= n_therm, h->stream));
+            a.program = llr::kProgPass;
+            a.pass_kind = 0;
+            LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
+            a.pass_kind = 1;
+            for (int k = 0; k < h->n_or; ++k) LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
+            a.program = llr::kProgFinish;
+            a.measure = j >= n_therm;
+            LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
         }
-        LLR_CUDA(llr::launch_plain_update(a, i, h->stream));
+        a.program = llr::kProgUpdate;
+        LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
     }
     LLR_CUDA(cudaMemcpyAsync(a_inout, h->d_a, sizeof(double) * (size_t)h->n,
                              cudaMemcpyDeviceToHost, h->stream));
@@ -433,7 +469,7 @@ int llr_status(llr_handle h, int *out)
     std::vector<LatState> st;
     if (int r = pull_states(h, st)) return r;
     for (int i = 0; i < h->n; ++i) out[i] = st[(size_t)i].status;
-    return LLR_OK;
+    return check_queue(h);
 }
 
 int llr_set_kernel_config(llr_handle h, int threads, int fast_math)
@@ -441,8 +477,8 @@ int llr_set_kernel_config(llr_handle h, int threads, int fast_math)
     if (int r = check_handle(h)) return r;
     if (threads != 128 && threads != 256 && threads != 512)
         return fail(LLR_ERR_ARG, "threads must be 128, 256 or 512");
-    h->threads = threads;
-    h->fast_math = fast_math != 0;
+    h->cfg.threads = threads;
+    h->cfg.fast_math = fast_math != 0;
     return LLR_OK;
 }
 
@@ -457,6 +493,8 @@ int llr_destroy(llr_handle h)
     cudaFree(h->d_mean);
     cudaFree(h->d_int);
     cudaFree(h->d_links);
+    cudaFree(h->d_sync);
+    cudaFree(h->d_order);
     delete h;
     return LLR_OK;
 }

@@ -11,21 +11,33 @@
 //   Algorithm 1   n_therm + n_meas sweeps, measure after n_therm
 //   eq. kk21      a <- a + 12 <<dE>> / (dE^2 (n + 1))
 //
-// Design (one CTA owns one lattice for the whole launch):
-//   * links are float32 angles, SoA by (direction, site parity), sites of a
-//     parity in lexicographic order: theta[off + (2 mu + p) * V/2 + s/2];
-//   * a class (mu, p) is updated in chunks of NT consecutive links: every
-//     thread builds the 6 staples of its link from 18 neighbour angles and
-//     draws its proposal (von Mises heat-bath, Best & Fisher 1979, or the
-//     reflection theta' = -theta - 2 alpha), giving dE in FP32;
-//   * dE goes to int64 fixed point (2^-32); each warp forms inclusive
-//     prefix sums; warp 0 then walks the chunk in link order, deciding each
-//     block of B links with the restricted Metropolis rule
-//     dist(E + dE_block) <= dist(E), using a ballot to find the first
-//     rejected block among 32 speculatively accepted ones;
-//   * accepted angles are written back; after 1 + n_or passes the CTA sums
-//     the 6V plaquettes (exact float32 angle sums + cosf, fixed-point
-//     accumulation) and resynchronises the tracked energy.
+// Design
+//   * Links are float32 angles, SoA by (direction, site parity), sites of a
+//     parity in lexicographic order: theta[off + (2 mu + p) * V/2 + s/2].
+//   * One persistent kernel.  Work items are (composite sweep j, lattice);
+//     a CTA takes the next item from an atomic counter, waits (bounded) until
+//     sweep j-1 of that lattice is done, and owns the lattice for that sweep.
+//     Items run sweep-major, so uneven lattice sizes balance across SMs.
+//   * In a heat-bath pass the warps are specialised: producer warps build
+//     the six staples of one link per thread from 18 neighbour angles, draw
+//     the von Mises proposal (Best & Fisher 1979) and its dE, convert dE to
+//     int64 fixed point
+//     (2^-32) and form warp prefix sums; a consumer warp walks the chunks in
+//     link order and decides each block of B links with the restricted
+//     Metropolis rule dist(E + dE_block) <= dist(E), using a ballot to find
+//     the first rejected block among 32 speculatively accepted ones, then
+//     writes the accepted angles.  Chunks pass through a 4-stage shared
+//     memory ring guarded by named barriers, so proposals for later chunks
+//     overlap with the scan of earlier ones.
+//   * Overrelaxation (theta' = -theta - 2 alpha) conserves E exactly, so its
+//     passes skip the scan: every warp reflects links and writes them
+//     directly.
+//   * The per-class update, energy and update functions are not inlined, so
+//     every program (batched sweeps, single passes, the plain form) runs the
+//     same machine code and gives bit-identical results.
+//   * After 1 + n_or passes the CTA sums the 6V plaquettes (float32 angles
+//     summed exactly as hi + lo, cosf, fixed-point accumulation) and
+//     resynchronises the tracked energy.
 #include <cstdio>
 
 #include "llr_internal.h"
@@ -34,6 +46,7 @@ namespace llr {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kStages = 4;
 
 // ---------------------------------------------------------------------------
 // Best & Fisher (1979) von Mises sampler, density ~ exp(kappa cos X).
@@ -46,11 +59,13 @@ constexpr unsigned kFull = 0xffffffffu;
 // full float precision.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool von_mises(float kappa, uint32_t c0, uint32_t c1, uint32_t c2,
-                                          uint32_t k0, uint32_t k1, float &X)
+                                          uint32_t k0, uint32_t k1, float &X, float &cX)
 {
     if (fabsf(kappa) < 1e-6f) {
         const U4 w = philox4x32_10(c0, c1, c2, 0u, k0, k1);
-        X = kPi * (2.0f * u01(w.x) - 1.0f);
+        const float t = 2.0f * u01(w.x) - 1.0f;
+        X = kPi * t;
+        cX = cospif(t);
         return true;
     }
     const float k = fabsf(kappa);
@@ -81,6 +96,7 @@ __device__ __forceinline__ bool von_mises(float kappa, uint32_t c0, uint32_t c1,
             float x = u3 > 0.5f ? mag : -mag;
             if (kappa < 0.0f) x = wrap_angle(x + kPi);
             X = x;
+            cX = kappa < 0.0f ? -f : f;
             return true;
         }
     }
@@ -100,9 +116,9 @@ __device__ __forceinline__ void sin_cos(float x, float *s, float *c)
 __device__ __forceinline__ int decode_half(int h, int p, int L, uint32_t magic, int x[4])
 {
     const int n = 2 * h;
-    int q = (int)__umulhi((uint32_t)n, magic);
+    const int q = (int)__umulhi((uint32_t)n, magic);
     const int x0e = n - q * L;
-    int q2 = (int)__umulhi((uint32_t)q, magic);
+    const int q2 = (int)__umulhi((uint32_t)q, magic);
     x[1] = q - q2 * L;
     const int q3 = (int)__umulhi((uint32_t)q2, magic);
     x[2] = q2 - q3 * L;
@@ -116,9 +132,11 @@ __device__ __forceinline__ int decode_half(int h, int p, int L, uint32_t magic, 
 // forward  phi = theta_nu(x+mu) - theta_mu(x+nu) - theta_nu(x)
 // backward phi = theta_nu(x-nu) - theta_nu(x-nu+mu) - theta_mu(x-nu)
 // so that the link's local energy is sum_j cos(theta + phi_j) = Re(e^{i theta} S).
+// Plain (coherent) loads: other classes of this lattice were written earlier
+// in the same launch.
 template <int MU, bool FAST>
-__device__ __forceinline__ void staple_sum(const float *__restrict__ th, int half, int L,
-                                           const int x[4], int s, int p, float &Sr, float &Si)
+__device__ __forceinline__ void staple_sum(const float *th, int half, int L, const int x[4], int s,
+                                           int p, float &Sr, float &Si)
 {
     const int st[4] = {1, L, L * L, L * L * L};
     const int dmu = (x[MU] == L - 1) ? -(L - 1) * st[MU] : st[MU];
@@ -137,12 +155,12 @@ __device__ __forceinline__ void staple_sum(const float *__restrict__ th, int hal
         const int smnu_pmu = smnu + dmu;
         const float *thnu_p = th + (2 * nu + p) * half;
         const float *thnu_q = th + (2 * nu + q) * half;
-        const float a1 = __ldg(thnu_q + (spmu >> 1));      // theta_nu(x+mu)
-        const float a2 = __ldg(thmu_q + (spnu >> 1));      // theta_mu(x+nu)
-        const float a3 = __ldg(thnu_p + (s >> 1));         // theta_nu(x)
-        const float b1 = __ldg(thnu_p + (smnu_pmu >> 1));  // theta_nu(x-nu+mu)
-        const float b2 = __ldg(thmu_q + (smnu >> 1));      // theta_mu(x-nu)
-        const float b3 = __ldg(thnu_q + (smnu >> 1));      // theta_nu(x-nu)
+        const float a1 = thnu_q[spmu >> 1];      // theta_nu(x+mu)
+        const float a2 = thmu_q[spnu >> 1];      // theta_mu(x+nu)
+        const float a3 = thnu_p[s >> 1];         // theta_nu(x)
+        const float b1 = thnu_p[smnu_pmu >> 1];  // theta_nu(x-nu+mu)
+        const float b2 = thmu_q[smnu >> 1];      // theta_mu(x-nu)
+        const float b3 = thnu_q[smnu >> 1];      // theta_nu(x-nu)
         const float pf = a1 - a2 - a3;
         const float pb = b3 - b1 - b2;
         float sf, cf, sb, cb;
@@ -153,64 +171,74 @@ __device__ __forceinline__ void staple_sum(const float *__restrict__ th, int hal
     }
 }
 
-template <int NT>
-struct Smem {
-    LatState st;
-    long long P[NT];
-    long long bs[NT];
-    unsigned endmask[NT / 32];
-    unsigned accmask[NT / 32];
-    long long red[NT / 32];
-    unsigned long long acc_cnt;
-    unsigned long long cap_cnt;
+// Named barriers 1..8 (0 is __syncthreads): stage s is full (1 + s) / empty (5 + s).
+__device__ __forceinline__ void bar_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+template <int NWP>
+struct Stage {
+    float thn[NWP * 32];
+    long long P[NWP * 32];
+    long long bs[NWP * 32];
+    unsigned endmask[NWP];
 };
 
-// One checkerboard class (MU, p).  kind 0: heat-bath at slope a_f with
-// Philox tag `tag`; kind 1: overrelaxation.
-template <int MU, int NT, bool FAST>
-__device__ void class_update(Smem<NT> &sm, float *__restrict__ th, int p, int kind, float a_f,
-                             uint32_t tag, int B)
+template <int NWP>
+struct Smem {
+    LatState st;
+    Stage<NWP> stage[kStages];
+    long long red[NWP + 1];
+    unsigned long long acc_cnt;
+    unsigned long long cap_cnt;
+    int item_lat, item_j, item_state;
+};
+
+// Producer side of one heat-bath class (MU, p): proposals and warp prefix
+// sums, chunk by chunk, into the stage ring (slope a_f, Philox tag `tag`).
+template <int MU, int NWP, bool FAST>
+__device__ __noinline__ void produce_class(Smem<NWP> &sm, const float *th, int p, float a_f, uint32_t tag,
+                              int B, int nchunk)
 {
+    constexpr int NT = (NWP + 1) * 32, CH = NWP * 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int L = sm.st.L, half = sm.st.half;
     const uint32_t magic = sm.st.magic, V = 2u * (uint32_t)half;
     const uint32_t k0 = sm.st.key0, k1 = sm.st.key1, sweep = sm.st.sweep;
-    float *own = th + (2 * MU + p) * half;
-    const int nchunk = (half + NT - 1) / NT;
+    const float *own = th + (2 * MU + p) * half;
     for (int ch = 0; ch < nchunk; ++ch) {
-        const int h = ch * NT + tid;
+        const int s = ch & (kStages - 1);
+        if (ch >= kStages) bar_sync(5 + s, NT);
+        const int h = ch * CH + tid;
         const bool valid = h < half;
         float thn = 0.0f;
         long long d = 0;
         if (valid) {
             int x[4];
-            const int s = decode_half(h, p, L, magic, x);
+            const int site = decode_half(h, p, L, magic, x);
             float Sr, Si;
-            staple_sum<MU, FAST>(th, half, L, x, s, p, Sr, Si);
+            staple_sum<MU, FAST>(th, half, L, x, site, p, Sr, Si);
             const float t0 = own[h];
             float so, co;
-            sin_cos<FAST>(t0, &so, &co);
-            const float e_old = co * Sr - so * Si;
+            sincosf(t0, &so, &co);   // accurate: a biased cosine here biases every dE
+            const float e_old = co * Sr - so * Si;     // |S| cos(theta + alpha)
             const float alpha = atan2f(Si, Sr);
-            if (kind == 0) {
-                const float Sabs = sqrtf(Sr * Sr + Si * Si);
-                float X;
-                const uint32_t link = (uint32_t)MU * V + (uint32_t)s;
-                if (von_mises(-a_f * Sabs, link, sweep, tag, k0, k1, X)) {
-                    thn = wrap_angle(X - alpha);
-                } else {
-                    thn = t0;
-                    atomicAdd(&sm.cap_cnt, 1ull);
-                }
+            const float Sabs = sqrtf(Sr * Sr + Si * Si);
+            float X, cX;
+            const uint32_t link = (uint32_t)MU * V + (uint32_t)site;
+            if (von_mises(-a_f * Sabs, link, sweep, tag, k0, k1, X, cX)) {
+                thn = wrap_angle(X - alpha);
+                d = to_fx(Sabs * cX - e_old);            // theta' + alpha = X
             } else {
-                thn = wrap_angle(-t0 - 2.0f * alpha);
+                thn = t0;
+                atomicAdd(&sm.cap_cnt, 1ull);
             }
-            float sn, cn;
-            sin_cos<FAST>(thn, &sn, &cn);
-            const float e_new = cn * Sr - sn * Si;
-            d = to_fx(e_new - e_old);
         }
-        // warp-inclusive prefix sums of the fixed-point dE
         long long P = d;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -222,85 +250,137 @@ __device__ void class_update(Smem<NT> &sm, float *__restrict__ th, int p, int ki
         const long long bsum = P - (bstart > 0 ? Pprev : 0ll);
         const bool isend = valid && (((lane & (B - 1)) == B - 1) || h == half - 1);
         const unsigned em = __ballot_sync(kFull, isend);
-        sm.P[tid] = P;
-        sm.bs[tid] = bsum;
-        if (lane == 0) sm.endmask[warp] = em;
-        __syncthreads();
-        if (warp == 0) {
-            // sequential Metropolis accept of the chunk's blocks in link order
-            long long E = sm.st.E_fx;
-            const long long lo = sm.st.lo_fx, hi = sm.st.hi_fx;
-            for (int g = 0; g < NT / 32; ++g) {
-                unsigned rem = sm.endmask[g];
-                unsigned acc = 0u;
-                const long long Pk = sm.P[g * 32 + lane];
-                const long long bk = sm.bs[g * 32 + lane];
-                long long base = 0;
-                while (rem) {
-                    const long long Ea = E + (Pk - base);
-                    const long long Eb = Ea - bk;
-                    const bool mine = (rem >> lane) & 1u;
-                    const bool viol = mine && (dist_fx(Ea, lo, hi) > dist_fx(Eb, lo, hi));
-                    const unsigned vm = __ballot_sync(kFull, viol);
-                    if (vm == 0u) {
-                        const int last = 31 - __clz(rem);
-                        E += __shfl_sync(kFull, Pk, last) - base;
-                        acc |= rem;
-                        rem = 0u;
-                    } else {
-                        const int j = __ffs(vm) - 1;
-                        acc |= rem & ((1u << j) - 1u);
-                        const long long Pj = __shfl_sync(kFull, Pk, j);
-                        const long long bj = __shfl_sync(kFull, bk, j);
-                        E += (Pj - bj) - base;   // energy before the rejected block
-                        base = Pj;               // skip its contribution
-                        rem &= ~((2u << j) - 1u);
-                    }
-                }
-                if (lane == 0) sm.accmask[g] = acc;
-            }
-            if (lane == 0) sm.st.E_fx = E;
-        }
-        __syncthreads();
-        // write back the accepted proposals
-        bool accepted = false;
-        if (valid) {
-            const unsigned e = sm.endmask[warp] & ~((1u << lane) - 1u);
-            const int eb = __ffs(e) - 1;
-            accepted = (sm.accmask[warp] >> eb) & 1u;
-            if (accepted) own[h] = thn;
-        }
-        const unsigned am = __ballot_sync(kFull, accepted);
-        if (lane == 0 && am) atomicAdd(&sm.acc_cnt, (unsigned long long)__popc(am));
+        Stage<NWP> &stg = sm.stage[s];
+        stg.thn[tid] = thn;
+        stg.P[tid] = P;
+        stg.bs[tid] = bsum;
+        if (lane == 0) stg.endmask[warp] = em;
+        bar_arrive(1 + s, NT);
     }
-    __syncthreads();
 }
 
-template <int NT, bool FAST>
-__device__ void full_pass(Smem<NT> &sm, float *th, int kind, float a_f, uint32_t tag, int B,
-                          int class_mask = 0xFF)
+// One overrelaxation class (MU, p): theta' = -theta - 2 alpha keeps
+// |S| cos(theta + alpha), so E is unchanged in exact arithmetic and the move
+// is always inside the window; every link is written directly by every warp
+// (the float32 rounding of E, ~1e-6 per link, is absorbed by the resync at
+// the end of the composite sweep).
+template <int MU, int NWP, bool FAST>
+__device__ __noinline__ void overrelax_class(Smem<NWP> &sm, float *th, int p)
 {
+    constexpr int NT = (NWP + 1) * 32;
+    const int L = sm.st.L, half = sm.st.half;
+    const uint32_t magic = sm.st.magic;
+    float *own = th + (2 * MU + p) * half;
+    for (int h = threadIdx.x; h < half; h += NT) {
+        int x[4];
+        const int site = decode_half(h, p, L, magic, x);
+        float Sr, Si;
+        staple_sum<MU, FAST>(th, half, L, x, site, p, Sr, Si);
+        own[h] = wrap_angle(-own[h] - 2.0f * atan2f(Si, Sr));
+    }
+}
+
+// Consumer side: sequential Metropolis accept of the chunk's blocks in link
+// order, then the write of the accepted angles.  Runs in the last warp.
+template <int NWP>
+__device__ __noinline__ void consume_class(Smem<NWP> &sm, float *own, int half, int nchunk)
+{
+    constexpr int NT = (NWP + 1) * 32, CH = NWP * 32;
+    const int lane = threadIdx.x & 31;
+    long long E = sm.st.E_fx;
+    const long long lo = sm.st.lo_fx, hi = sm.st.hi_fx;
+    unsigned cnt = 0;
+    for (int ch = 0; ch < nchunk; ++ch) {
+        const int s = ch & (kStages - 1);
+        bar_sync(1 + s, NT);
+        const Stage<NWP> &stg = sm.stage[s];
+        for (int g = 0; g < NWP; ++g) {
+            const unsigned em = stg.endmask[g];
+            unsigned rem = em, acc = 0u;
+            const long long Pk = stg.P[g * 32 + lane];
+            const long long bk = stg.bs[g * 32 + lane];
+            long long base = 0;
+            while (rem) {
+                const long long Ea = E + (Pk - base);
+                const long long Eb = Ea - bk;
+                const bool mine = (rem >> lane) & 1u;
+                const bool viol = mine && (dist_fx(Ea, lo, hi) > dist_fx(Eb, lo, hi));
+                const unsigned vm = __ballot_sync(kFull, viol);
+                if (vm == 0u) {
+                    const int last = 31 - __clz(rem);
+                    E += __shfl_sync(kFull, Pk, last) - base;
+                    acc |= rem;
+                    rem = 0u;
+                } else {
+                    const int j = __ffs(vm) - 1;
+                    acc |= rem & ((1u << j) - 1u);
+                    const long long Pj = __shfl_sync(kFull, Pk, j);
+                    const long long bj = __shfl_sync(kFull, bk, j);
+                    E += (Pj - bj) - base;   // energy before the rejected block
+                    base = Pj;               // skip its contribution
+                    rem &= ~((2u << j) - 1u);
+                }
+            }
+            const int h = ch * CH + g * 32 + lane;
+            if (h < half) {
+                const int eb = __ffs(em & ~((1u << lane) - 1u)) - 1;
+                if ((acc >> eb) & 1u) {
+                    own[h] = stg.thn[g * 32 + lane];
+                    ++cnt;
+                }
+            }
+        }
+        if (ch + kStages < nchunk) bar_arrive(5 + s, NT);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
+    if (lane == 0) {
+        sm.st.E_fx = E;
+        sm.acc_cnt += cnt;
+    }
+}
+
+template <int NWP, bool FAST>
+__device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t tag, int B,
+                         int class_mask)
+{
+    constexpr int CH = NWP * 32;
     if (threadIdx.x == 0) sm.acc_cnt = 0ull;
     __syncthreads();
+    const int half = sm.st.half;
+    const int nchunk = (half + CH - 1) / CH;
+    const bool consumer = (threadIdx.x >> 5) == NWP;
 #pragma unroll 1
     for (int cls = 0; cls < 8; ++cls) {
         if (!((class_mask >> cls) & 1)) continue;
-        const int p = cls & 1;
-        switch (cls >> 1) {
-            case 0: class_update<0, NT, FAST>(sm, th, p, kind, a_f, tag, B); break;
-            case 1: class_update<1, NT, FAST>(sm, th, p, kind, a_f, tag, B); break;
-            case 2: class_update<2, NT, FAST>(sm, th, p, kind, a_f, tag, B); break;
-            default: class_update<3, NT, FAST>(sm, th, p, kind, a_f, tag, B); break;
+        const int mu = cls >> 1, p = cls & 1;
+        if (kind == 1) {
+            switch (mu) {
+                case 0: overrelax_class<0, NWP, FAST>(sm, th, p); break;
+                case 1: overrelax_class<1, NWP, FAST>(sm, th, p); break;
+                case 2: overrelax_class<2, NWP, FAST>(sm, th, p); break;
+                default: overrelax_class<3, NWP, FAST>(sm, th, p); break;
+            }
+        } else if (consumer) {
+            consume_class<NWP>(sm, th + (2 * mu + p) * half, half, nchunk);
+        } else {
+            switch (mu) {
+                case 0: produce_class<0, NWP, FAST>(sm, th, p, a_f, tag, B, nchunk); break;
+                case 1: produce_class<1, NWP, FAST>(sm, th, p, a_f, tag, B, nchunk); break;
+                case 2: produce_class<2, NWP, FAST>(sm, th, p, a_f, tag, B, nchunk); break;
+                default: produce_class<3, NWP, FAST>(sm, th, p, a_f, tag, B, nchunk); break;
+            }
         }
+        __syncthreads();   // the next class reads the angles written here
     }
     if (threadIdx.x == 0) {
         const unsigned long long n =
-            (unsigned long long)__popc(class_mask & 0xFF) * (unsigned long long)sm.st.half;
+            (unsigned long long)__popc(class_mask & 0xFF) * (unsigned long long)half;
         if (kind == 0) {
             sm.st.hb_acc += sm.acc_cnt;
             sm.st.hb_tot += n;
         } else {
-            sm.st.or_acc += sm.acc_cnt;
+            sm.st.or_acc += n;
             sm.st.or_tot += n;
         }
     }
@@ -329,10 +409,11 @@ __device__ __forceinline__ float plaquette_cos(float a, float b, float c, float 
 }
 
 // Fresh energy of the CTA's lattice in fixed point: sum over the 6 V
-// plaquettes, exact int64 accumulation and reduction.
-template <int NT>
-__device__ long long fresh_energy_fx(Smem<NT> &sm, const float *__restrict__ th)
+// plaquettes, exact int64 accumulation and reduction.  Valid in thread 0.
+template <int NWP>
+__device__ __noinline__ long long fresh_energy_fx(Smem<NWP> &sm, const float *th)
 {
+    constexpr int NT = (NWP + 1) * 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int L = sm.st.L, half = sm.st.half;
     const uint32_t magic = sm.st.magic;
@@ -341,9 +422,9 @@ __device__ long long fresh_energy_fx(Smem<NT> &sm, const float *__restrict__ th)
     long long acc = 0;
     for (int s = tid; s < V; s += NT) {
         int x[4];
-        int q = (int)__umulhi((uint32_t)s, magic);
+        const int q = (int)__umulhi((uint32_t)s, magic);
         x[0] = s - q * L;
-        int q2 = (int)__umulhi((uint32_t)q, magic);
+        const int q2 = (int)__umulhi((uint32_t)q, magic);
         x[1] = q - q2 * L;
         const int q3 = (int)__umulhi((uint32_t)q2, magic);
         x[2] = q2 - q3 * L;
@@ -354,15 +435,15 @@ __device__ long long fresh_energy_fx(Smem<NT> &sm, const float *__restrict__ th)
         int sp[4];
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
-            t[mu] = __ldg(th + (2 * mu + p) * half + hs);
+            t[mu] = th[(2 * mu + p) * half + hs];
             sp[mu] = s + ((x[mu] == L - 1) ? -(L - 1) * st[mu] : st[mu]);
         }
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu)
 #pragma unroll
             for (int nu = mu + 1; nu < 4; ++nu) {
-                const float tnu_xmu = __ldg(th + (2 * nu + (p ^ 1)) * half + (sp[mu] >> 1));
-                const float tmu_xnu = __ldg(th + (2 * mu + (p ^ 1)) * half + (sp[nu] >> 1));
+                const float tnu_xmu = th[(2 * nu + (p ^ 1)) * half + (sp[mu] >> 1)];
+                const float tmu_xnu = th[(2 * mu + (p ^ 1)) * half + (sp[nu] >> 1)];
                 acc += to_fx(plaquette_cos(t[mu], tnu_xmu, tmu_xnu, t[nu]));
             }
     }
@@ -372,23 +453,22 @@ __device__ long long fresh_energy_fx(Smem<NT> &sm, const float *__restrict__ th)
     __syncthreads();
     long long tot = 0;
     if (tid == 0)
-        for (int w = 0; w < NT / 32; ++w) tot += sm.red[w];
-    return tot;   // valid in thread 0 only
+        for (int w = 0; w < NWP + 1; ++w) tot += sm.red[w];
+    __syncthreads();
+    return tot;
 }
 
 // Resync after a composite sweep; thread 0 updates the state.
-template <int NT>
-__device__ void end_of_sweep(Smem<NT> &sm, const float *th, bool measure, bool count_sweep)
+template <int NWP>
+__device__ void end_of_sweep(Smem<NWP> &sm, const float *th, bool measure)
 {
-    const long long fresh = fresh_energy_fx<NT>(sm, th);
+    const long long fresh = fresh_energy_fx<NWP>(sm, th);
     if (threadIdx.x == 0) {
         const double drift = fabs((double)(sm.st.E_fx - fresh) * kInvFx);
         if (drift > sm.st.max_drift) sm.st.max_drift = drift;
         sm.st.E_fx = fresh;
-        if (count_sweep) {
-            sm.st.sweep += 1u;
-            sm.st.sweeps_done += 1ull;
-        }
+        sm.st.sweep += 1u;
+        sm.st.sweeps_done += 1ull;
         if (measure) {
             const double dEm = (double)fresh * kInvFx - (sm.st.E_lo + 0.5 * sm.st.dE);
             sm.st.sum_dE += dEm;
@@ -399,130 +479,176 @@ __device__ void end_of_sweep(Smem<NT> &sm, const float *th, bool measure, bool c
     __syncthreads();
 }
 
-template <int NT, bool FAST>
-__device__ void composite_sweep(Smem<NT> &sm, float *th, float a_f, uint32_t tag, int n_or,
+template <int NWP, bool FAST>
+__device__ void composite_sweep(Smem<NWP> &sm, float *th, float a_f, uint32_t tag, int n_or,
                                 int B, bool measure)
 {
-    full_pass<NT, FAST>(sm, th, 0, a_f, tag, B);
-    for (int k = 0; k < n_or; ++k) full_pass<NT, FAST>(sm, th, 1, a_f, tag, B);
-    end_of_sweep<NT>(sm, th, measure, true);
+    run_pass<NWP, FAST>(sm, th, 0, a_f, tag, B, 0xFF);
+    for (int k = 0; k < n_or; ++k) run_pass<NWP, FAST>(sm, th, 1, a_f, tag, B, 0xFF);
+    end_of_sweep<NWP>(sm, th, measure);
 }
 
-template <int NT, bool FAST>
-__global__ void __launch_bounds__(NT) chain_kernel(ChainArgs args)
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    __shared__ Smem<NT> sm;
-    const int lat = args.order ? args.order[blockIdx.x] : (int)blockIdx.x;
-    if (threadIdx.x == 0) {
-        sm.st = args.lats[lat];
-        sm.cap_cnt = 0ull;
-        if (args.mode == kModePass && args.a_in) sm.st.a = args.a_in[lat];
-        if (args.mode == kModeSweeps || args.mode == kModeRM) {
-            if (args.a_in) sm.st.a = args.a_in[lat];
-            sm.st.sum_dE = 0.0;
-            sm.st.sum_dE2 = 0.0;
-            sm.st.n_meas = 0;
-        }
-    }
-    __syncthreads();
-    float *th = args.theta + sm.st.off;
-
-    if (args.mode == kModeResync) {
-        const long long fresh = fresh_energy_fx<NT>(sm, th);
-        if (threadIdx.x == 0) sm.st.E_fx = fresh;
-    } else if (args.mode == kModePass) {
-        full_pass<NT, FAST>(sm, th, args.pass_kind, (float)sm.st.a, kTagSweep, args.block,
-                            args.class_mask);
-    } else if (args.mode == kModeApproach) {
-        int n = 0;
-        for (;;) {
-            const long long E = sm.st.E_fx;   // uniform after the last barrier
-            if (dist_fx(E, sm.st.lo_fx, sm.st.hi_fx) == 0) break;
-            if (n >= args.max_approach) {
-                if (threadIdx.x == 0) sm.st.status = -3;   // LLR_ERR_WINDOW
-                break;
-            }
-            const float a_f = (float)(E < sm.st.lo_fx ? -args.beta_up : -args.beta_dn);
-            composite_sweep<NT, FAST>(sm, th, a_f, kTagApproach, args.n_or, args.block, false);
-            ++n;
-        }
-        if (threadIdx.x == 0 && args.approach_sweeps) args.approach_sweeps[lat] = n;
-    } else {
-        const float a_f = (float)sm.st.a;
-        const int total = args.n_therm + args.n_meas;
-        for (int j = 0; j < total; ++j)
-            composite_sweep<NT, FAST>(sm, th, a_f, kTagSweep, args.n_or, args.block,
-                                      args.measure && j >= args.n_therm);
-        if (threadIdx.x == 0) {
-            if (args.mode == kModeRM) {
-                const double mean = sm.st.n_meas > 0 ? sm.st.sum_dE / sm.st.n_meas : 0.0;
-                const double a_new =
-                    sm.st.a + 12.0 * mean / (sm.st.dE * sm.st.dE * (double)(args.rm_index + 1));
-                if (!isfinite(a_new)) sm.st.status = -5;   // LLR_ERR_NUMERIC
-                sm.st.a = a_new;
-                if (args.a_out) args.a_out[lat] = a_new;
-                if (args.mean_out) args.mean_out[lat] = mean;
-            } else if (args.mean_out) {
-                args.mean_out[lat] = sm.st.sum_dE;
-            }
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        sm.st.caps += sm.cap_cnt;
-        args.lats[lat] = sm.st;
-    }
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-// ---------------------------------------------------------------------------
-// Plain form: one lattice per launch, one launch per pass / resync / update.
-// ---------------------------------------------------------------------------
-template <int NT>
-__global__ void __launch_bounds__(NT) plain_pass_kernel(ChainArgs args, int lat, int kind,
-                                                        float a_f)
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 {
-    __shared__ Smem<NT> sm;
-    if (threadIdx.x == 0) {
-        sm.st = args.lats[lat];
-        sm.cap_cnt = 0ull;
-    }
-    __syncthreads();
-    float *th = args.theta + sm.st.off;
-    full_pass<NT, true>(sm, th, kind, a_f, kTagSweep, args.block);
-    if (threadIdx.x == 0) {
-        sm.st.caps += sm.cap_cnt;
-        args.lats[lat] = sm.st;
-    }
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) plain_finish_kernel(ChainArgs args, int lat, int measure)
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
 {
-    __shared__ Smem<NT> sm;
-    if (threadIdx.x == 0) sm.st = args.lats[lat];
-    __syncthreads();
-    end_of_sweep<NT>(sm, args.theta + sm.st.off, measure != 0, true);
-    if (threadIdx.x == 0) args.lats[lat] = sm.st;
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__global__ void plain_begin_kernel(ChainArgs args, int lat)
+// Robbins-Monro update of the CTA's lattice (thread 0).
+__device__ __noinline__ void rm_update(LatState &st, const KernelArgs &args, int lat)
 {
-    LatState &st = args.lats[lat];
-    if (args.a_in) st.a = args.a_in[lat];
-    st.sum_dE = 0.0;
-    st.sum_dE2 = 0.0;
-    st.n_meas = 0;
-}
-
-__global__ void plain_update_kernel(ChainArgs args, int lat)
-{
-    LatState &st = args.lats[lat];
     const double mean = st.n_meas > 0 ? st.sum_dE / st.n_meas : 0.0;
     const double a_new = st.a + 12.0 * mean / (st.dE * st.dE * (double)(args.rm_index + 1));
-    if (!isfinite(a_new)) st.status = -5;
+    if (!isfinite(a_new)) st.status = -5;   // LLR_ERR_NUMERIC
     st.a = a_new;
     if (args.a_out) args.a_out[lat] = a_new;
     if (args.mean_out) args.mean_out[lat] = mean;
+}
+
+// Resident CTAs per SM the register budget is held to (80 registers at 256 threads).
+template <int NWP>
+constexpr int min_ctas() { return NWP == 3 ? 6 : (NWP == 7 ? 3 : 1); }
+
+template <int NWP, bool FAST>
+__global__ void __launch_bounds__((NWP + 1) * 32, min_ctas<NWP>()) llr_kernel(KernelArgs args)
+{
+    __shared__ Smem<NWP> sm;
+    const int tid = threadIdx.x;
+    const bool multi = args.program == kProgSweeps || args.program == kProgRM;
+    const int per_lat = multi ? args.n_therm + args.n_meas : 1;
+    const unsigned n_items = (unsigned)args.n_lat * (unsigned)per_lat;
+    unsigned *counter = args.sync;
+    unsigned *err = args.sync + 1;
+    unsigned *done = args.sync + 2;
+    for (;;) {
+        if (tid == 0) {
+            const unsigned i = atomicAdd(counter, 1u);
+            int state = 0;
+            if (i < n_items) {
+                const int j = (int)(i / (unsigned)args.n_lat);
+                const int slot = (int)(i % (unsigned)args.n_lat);
+                state = 1;
+                if (j > 0) {
+                    // sweep j-1 of this lattice was dequeued earlier by a running
+                    // CTA; wait for it, but never longer than wait_limit_ns
+                    const unsigned long long t0 = global_ns();
+                    while (ld_acquire(done + slot) < (unsigned)j) {
+                        if (global_ns() - t0 > args.wait_limit_ns) {
+                            atomicOr(err, 1u);
+                            state = 2;
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                }
+                sm.item_lat = slot;
+                sm.item_j = j;
+                if (state == 1) sm.st = args.lats[args.order ? args.order[slot] : slot];
+            }
+            sm.item_state = state;
+            sm.cap_cnt = 0ull;
+        }
+        __syncthreads();
+        const int state = sm.item_state;
+        if (state == 0) break;
+        if (state == 2) {
+            __syncthreads();
+            continue;   // timed out: leave this lattice alone, the host reads the error word
+        }
+        const int slot = sm.item_lat, j = sm.item_j;
+        const int lat = args.order ? args.order[slot] : slot;
+        float *th = args.theta + sm.st.off;
+
+        switch (args.program) {
+            case kProgSweeps:
+            case kProgRM: {
+                if (j == 0 && tid == 0) {
+                    if (args.a_in) sm.st.a = args.a_in[lat];
+                    sm.st.sum_dE = 0.0;
+                    sm.st.sum_dE2 = 0.0;
+                    sm.st.n_meas = 0;
+                }
+                __syncthreads();
+                const float a_f = (float)sm.st.a;
+                composite_sweep<NWP, FAST>(sm, th, a_f, kTagSweep, args.n_or, args.block,
+                                           args.measure && j >= args.n_therm);
+                if (j == per_lat - 1 && tid == 0) {
+                    if (args.program == kProgRM)
+                        rm_update(sm.st, args, lat);
+                    else if (args.mean_out)
+                        args.mean_out[lat] = sm.st.sum_dE;
+                }
+                break;
+            }
+            case kProgApproach: {
+                int n = 0;
+                for (;;) {
+                    const long long E = sm.st.E_fx;   // uniform after the last barrier
+                    if (dist_fx(E, sm.st.lo_fx, sm.st.hi_fx) == 0) break;
+                    if (n >= args.max_approach) {
+                        if (tid == 0) sm.st.status = -3;   // LLR_ERR_WINDOW
+                        break;
+                    }
+                    const float a_f = (float)(E < sm.st.lo_fx ? -args.beta_up : -args.beta_dn);
+                    composite_sweep<NWP, FAST>(sm, th, a_f, kTagApproach, args.n_or, args.block,
+                                               false);
+                    ++n;
+                }
+                if (tid == 0 && args.approach_sweeps) args.approach_sweeps[lat] = n;
+                break;
+            }
+            case kProgResync: {
+                const long long fresh = fresh_energy_fx<NWP>(sm, th);
+                if (tid == 0) sm.st.E_fx = fresh;
+                break;
+            }
+            case kProgPass: {
+                if (tid == 0 && args.a_in) sm.st.a = args.a_in[lat];
+                __syncthreads();
+                run_pass<NWP, FAST>(sm, th, args.pass_kind, (float)sm.st.a, kTagSweep,
+                                    args.block, args.class_mask);
+                break;
+            }
+            case kProgBegin: {
+                if (tid == 0) {
+                    if (args.a_in) sm.st.a = args.a_in[lat];
+                    sm.st.sum_dE = 0.0;
+                    sm.st.sum_dE2 = 0.0;
+                    sm.st.n_meas = 0;
+                }
+                break;
+            }
+            case kProgFinish:
+                end_of_sweep<NWP>(sm, th, args.measure != 0);
+                break;
+            case kProgUpdate:
+                if (tid == 0) rm_update(sm.st, args, lat);
+                break;
+            default:
+                break;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            sm.st.caps += sm.cap_cnt;
+            args.lats[lat] = sm.st;
+            __threadfence();
+            st_release(done + slot, (unsigned)(j + 1));
+        }
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -614,47 +740,48 @@ __global__ void from_canonical_kernel(const LatState *lat, float *theta, const f
     }
 }
 
-template <int NT, bool FAST>
-cudaError_t launch_chain_t(const ChainArgs &a, cudaStream_t s)
+// Resident CTAs of one kernel variant (queried once per process and device).
+template <int NWP, bool FAST>
+int resident_ctas()
 {
-    chain_kernel<NT, FAST><<<a.n_lat, NT, 0, s>>>(a);
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (cached[dev] == 0) {
+        int per_sm = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, llr_kernel<NWP, FAST>,
+                                                      (NWP + 1) * 32, 0);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    }
+    return cached[dev];
+}
+
+template <int NWP, bool FAST>
+cudaError_t launch_t(const KernelArgs &a, cudaStream_t s)
+{
+    const bool multi = a.program == kProgSweeps || a.program == kProgRM;
+    const long long items = (long long)a.n_lat * (multi ? (a.n_therm + a.n_meas) : 1);
+    if (items <= 0) return cudaSuccess;
+    const long long cap = resident_ctas<NWP, FAST>();
+    const int grid = (int)(items < cap ? items : cap);
+    cudaError_t e = cudaMemsetAsync(a.sync, 0, sizeof(unsigned) * (size_t)(2 + a.n_lat), s);
+    if (e != cudaSuccess) return e;
+    llr_kernel<NWP, FAST><<<grid, (NWP + 1) * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_chain(const ChainArgs &a, int threads, bool fast_math, cudaStream_t s)
+cudaError_t launch_llr(const KernelArgs &a, const LaunchCfg &cfg, cudaStream_t s)
 {
     if (a.n_lat <= 0) return cudaSuccess;
-    if (threads == 128) return fast_math ? launch_chain_t<128, true>(a, s) : launch_chain_t<128, false>(a, s);
-    if (threads == 512) return fast_math ? launch_chain_t<512, true>(a, s) : launch_chain_t<512, false>(a, s);
-    return fast_math ? launch_chain_t<256, true>(a, s) : launch_chain_t<256, false>(a, s);
-}
-
-cudaError_t launch_plain_begin(const ChainArgs &a, int lattice, cudaStream_t s)
-{
-    plain_begin_kernel<<<1, 1, 0, s>>>(a, lattice);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_plain_pass(const ChainArgs &a, int lattice, int kind, double a_val,
-                              cudaStream_t s)
-{
-    plain_pass_kernel<256><<<1, 256, 0, s>>>(a, lattice, kind, (float)a_val);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_plain_finish(const ChainArgs &a, int lattice, int measure_this,
-                                cudaStream_t s)
-{
-    plain_finish_kernel<256><<<1, 256, 0, s>>>(a, lattice, measure_this);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_plain_update(const ChainArgs &a, int lattice, cudaStream_t s)
-{
-    plain_update_kernel<<<1, 1, 0, s>>>(a, lattice);
-    return cudaGetLastError();
+    if (cfg.threads == 128)
+        return cfg.fast_math ? launch_t<3, true>(a, s) : launch_t<3, false>(a, s);
+    if (cfg.threads == 512)
+        return cfg.fast_math ? launch_t<15, true>(a, s) : launch_t<15, false>(a, s);
+    return cfg.fast_math ? launch_t<7, true>(a, s) : launch_t<7, false>(a, s);
 }
 
 cudaError_t launch_hot_start(LatState *lats, float *theta, int n_lat, int max_half,

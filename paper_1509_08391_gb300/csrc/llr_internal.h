@@ -9,44 +9,50 @@
 
 namespace llr {
 
-enum ChainMode : int {
-    kModeSweeps = 0,    // n_therm + n_meas sweeps at fixed a, optional measurement
-    kModeRM = 1,        // the same, then the Robbins-Monro update of a
-    kModeApproach = 2,  // approach sweeps until E lies in the window
-    kModeResync = 3,    // fresh energy -> tracked energy, nothing else
-    kModePass = 4,      // one heat-bath (pass_kind 0) or overrelaxation (1) pass, no resync
+// Work programs of the persistent kernel.  Sweeps and RM create one work
+// item per (composite sweep, lattice); every other program one item per
+// lattice.
+enum Program : int {
+    kProgSweeps = 0,    // n_therm + n_meas composite sweeps at fixed a, optional measurement
+    kProgRM = 1,        // the same, then the Robbins-Monro update of a
+    kProgApproach = 2,  // approach sweeps until E lies in the window
+    kProgResync = 3,    // fresh energy -> tracked energy
+    kProgPass = 4,      // one heat-bath (pass_kind 0) or overrelaxation (1) pass, no resync
+    kProgBegin = 5,     // plain form: take a from a_in, clear the measurement
+    kProgFinish = 6,    // plain form: resync + optional measurement + sweep counter
+    kProgUpdate = 7,    // plain form: Robbins-Monro update from the accumulated measurement
 };
 
-struct ChainArgs {
+struct KernelArgs {
     LatState *lats;
     float *theta;
-    int n_lat;
-    int mode;
+    int n_lat;            // lattices in this launch (items per sweep)
+    const int *order;     // nullable: slot i is lattice order[i]
+    int program;
     int n_therm, n_meas, measure;
     int rm_index;
-    const double *a_in;   // nullable: use LatState::a
-    double *a_out;        // mode RM: new a;     nullable
-    double *mean_out;     // mode RM: <<dE>>; mode sweeps: sum of dE; nullable
+    const double *a_in;   // nullable: keep LatState::a
+    double *a_out;        // RM / update: new a (nullable)
+    double *mean_out;     // RM / update: <<dE>>; sweeps: sum of dE (nullable)
     int max_approach;
     double beta_up, beta_dn;
     int *approach_sweeps; // nullable
     int n_or;
     int block;            // window-accept block size B (power of two, <= 32)
-    const int *order;     // nullable: CTA i works on lattice order[i]
-    int pass_kind;        // mode pass: 0 heat-bath, 1 overrelaxation
-    int class_mask;       // mode pass: bit c selects class c = 2 mu + parity
+    int pass_kind;        // pass: 0 heat-bath, 1 overrelaxation
+    int class_mask;       // pass: bit c selects class c = 2 mu + parity
+    // work queue (device): [0] item counter, [1] error word, [2 ..] sweeps done per slot
+    unsigned *sync;
+    unsigned long long wait_limit_ns;   // bounded wait for a lattice's previous sweep
 };
 
-// Batched launch: one CTA per lattice, whole work of `mode` in one kernel.
-cudaError_t launch_chain(const ChainArgs &a, int threads, bool fast_math, cudaStream_t s);
+struct LaunchCfg {
+    int threads = 256;    // 128, 256 or 512: one consumer warp, the rest producers
+    bool fast_math = true;
+};
 
-// Plain form: single-lattice kernels, one launch per pass / resync / update.
-cudaError_t launch_plain_pass(const ChainArgs &a, int lattice, int kind, double a_val,
-                              cudaStream_t s);
-cudaError_t launch_plain_finish(const ChainArgs &a, int lattice, int measure_this,
-                                cudaStream_t s);
-cudaError_t launch_plain_update(const ChainArgs &a, int lattice, cudaStream_t s);
-cudaError_t launch_plain_begin(const ChainArgs &a, int lattice, cudaStream_t s);
+// Reset the work queue and launch the persistent kernel (stream ordered).
+cudaError_t launch_llr(const KernelArgs &a, const LaunchCfg &cfg, cudaStream_t s);
 
 // Hot start of every link of every lattice.
 cudaError_t launch_hot_start(LatState *lats, float *theta, int n_lat, int max_half,

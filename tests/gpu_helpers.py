@@ -57,21 +57,45 @@ def class_links(L, cls):
     return mu * V + s[par == p]
 
 
-def check_class_updates(b, w, lattices, a, kinds=(0, 1), classes=range(8)):
+def check_class_updates(b, w, lattices, a, kinds=(0, 1), classes=range(8), e_tie=1e-3):
     """Update one class at a time on the GPU and in the oracle from the same
-    state; every link of the class must agree within its tolerance."""
-    worst = 0.0
+    state.  Walking the class in update order, every link agrees within its
+    tolerance up to the first window decision that differs; that decision
+    must be a near tie (the oracle's candidate energy within e_tie of a window
+    edge, below the float32 error the GPU's running energy carries), and the
+    rest of that class is then not compared.  Returns (worst deviation, flips)."""
+    worst, flips = 0.0, 0
     for kind in kinds:
         for cls in classes:
             mirrors = {i: oracle_mirror(b, w, i) for i in lattices}
             S = {i: mirrors[i].staple_moduli() for i in lattices}
             b.single_pass(kind, a, class_mask=1 << cls)
             for i, o in mirrors.items():
-                o.class_pass(cls, kind, a[i])
-                d = np.abs(wrapped_diff(b.get_links(i), o.links()))
-                tol = link_tolerance(S[i])
+                tr = o.class_trace(cls, kind, a[i])
+                order = class_links(w.L[i], cls)
+                g = b.get_links(i).astype(np.float64)
+                d_all = np.abs(wrapped_diff(g, o.links()))
+                tol_all = link_tolerance(S[i])
+                # links outside the class must be untouched on both sides
+                outside = np.ones(g.size, bool)
+                outside[order] = False
+                assert np.all(d_all[outside] == 0.0) or np.all(d_all[outside] < 1e-7)
+                d = d_all[order]
+                tol = tol_all[order]
                 bad = np.nonzero(d > tol)[0]
-                assert bad.size == 0, ("kind", kind, "class", cls, "lattice", i,
-                                       [(float(d[k]), float(S[i][k])) for k in bad[:5]])
-                worst = max(worst, float(d.max()))
-    return worst
+                if bad.size:
+                    k = int(bad[0])
+                    gk = g[order][k]
+                    took_old = abs(wrapped_diff(gk, tr["th_old"][k])) <= tol[k]
+                    took_new = abs(wrapped_diff(gk, tr["th_prop"][k])) <= tol[k]
+                    flipped = (took_old and tr["accepted"][k]) or (took_new and not tr["accepted"][k])
+                    lo, hi = w.E_lo[i], w.E_lo[i] + w.dE[i]
+                    cand = tr["E_before"][k] + tr["dE"][k]
+                    margin = min(abs(cand - lo), abs(cand - hi))
+                    assert flipped and margin < e_tie, (
+                        "kind", kind, "class", cls, "lattice", i, "link", k, "dev", float(d[k]),
+                        "|S|", float(S[i][order][k]), "flipped", flipped, "margin", margin)
+                    flips += 1
+                    d = d[:k]
+                worst = max(worst, float(d.max()) if d.size else 0.0)
+    return worst, flips

@@ -34,7 +34,8 @@ def test_l20_class_updates_match_oracle_link_by_link():
         b.set_kernel_config(BENCH_THREADS, BENCH_FAST)
         b.sweep(np.full(2, -1.0), 2)         # leave the hot start
         a = np.array([-1.011, -0.99])
-        check_class_updates(b, w, [1], a, classes=[0, 5])
+        worst, flips = check_class_updates(b, w, [1], a, classes=[0, 5])
+        assert flips == 0
 
 
 def test_l20_full_batch_properties():
