@@ -45,6 +45,12 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--intervals", type=int, default=256)
+    p.add_argument("--converge", action="store_true",
+                   help="learned warm start vs naive start: RM-converged intervals/s")
+    p.add_argument("--target-L", type=int, default=20)
+    p.add_argument("--target-intervals", type=int, default=32)
+    p.add_argument("--target-replicas", type=int, default=4)
+    p.add_argument("--n-rm", type=int, default=150)
     return p.parse_args()
 
 
@@ -308,8 +314,74 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_converge(args):
+    """RM-converged intervals/s: batched learned warm start vs the plain form
+    from a naive start, at the target volume, on one GPU."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1509_08391_gb300 import build as bld
+    bld.build()
+    from paper_1509_08391_gb300 import llr, warmstart, workloads
+    t_all = time.perf_counter()
+    data = warmstart.training_set(n_int=24, replicas=2, n_rm=40, n_therm=args.n_therm,
+                                  n_meas=args.n_meas)
+    net, eps, loss = warmstart.fit_network(data)
+    L = args.target_L
+    target = workloads.warm_start_targets(L, replicas=args.target_replicas,
+                                          n_int=args.target_intervals)
+    res = warmstart.compare(target, net, eps, args.n_rm, args.n_therm, args.n_meas)
+    net.close()
+    n_int = args.target_intervals
+    conv_w = [s for s, ok in zip(res.warm_steps, res.agree_warm) if s is not None and ok]
+    conv_n = [s for s, ok in zip(res.naive_steps, res.agree_naive) if s is not None and ok]
+    # plain form: one lattice at a time with one launch per pass; timed on one
+    # lattice for one Robbins-Monro step, scaled by lattices and steps
+    w1 = workloads.subset(target, [0])
+    with llr.Batch.from_workload(w1, max_approach=1000) as b:
+        b.rm_step_plain(np.full(1, target.a0), args.n_therm, args.n_meas, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.rm_step_plain(np.full(1, target.a0), args.n_therm, args.n_meas, 1)
+        t_plain_lat_step = time.perf_counter() - t0
+    R = args.target_replicas
+    step_w = max(conv_w) if conv_w else None
+    step_n = max(conv_n) if conv_n else None
+    t_batched = res.seconds_per_step * (step_w if step_w else args.n_rm)
+    t_plain = t_plain_lat_step * target.n_lattices * (step_n if step_n else args.n_rm)
+    out = {
+        "metric": "RM-converged LLR intervals/s", "unit": "intervals/s",
+        "workload": target.name, "L": L, "intervals": n_int, "replicas": R,
+        "n_therm": args.n_therm, "n_meas": args.n_meas, "n_rm": args.n_rm,
+        "criterion": "replica-mean |a(n+1)-a(n)| <= 1e-4 for 3 steps and agreement with a "
+                     "2x-longer naive reference within 3 sigma",
+        "mlp": {"train_points": int(len(data["a"])), "train_seconds": data["seconds"],
+                "holdout_rms_L16": eps, "final_loss": loss, "gain_offset_n0": res.n0,
+                "start_error": {"warm": float(res.err_warm[0]), "naive": float(res.err_naive[0])},
+                "error_after_10": {"warm": float(res.err_warm[min(10, len(res.err_warm) - 1)]),
+                                   "naive": float(res.err_naive[min(10, len(res.err_naive) - 1)])}},
+        "batched_warm": {"converged": len(conv_w), "steps_to_all": step_w,
+                         "seconds_per_step": res.seconds_per_step,
+                         "intervals_per_s": len(conv_w) / t_batched if conv_w else 0.0},
+        "plain_naive": {"converged": len(conv_n), "steps_to_all": step_n,
+                        "seconds_per_lattice_step": t_plain_lat_step,
+                        "intervals_per_s": len(conv_n) / t_plain if conv_n else 0.0,
+                        "timing": "extrapolated from one lattice-step of the plain form"},
+        "median_steps": {"warm": float(np.median([s for s in res.warm_steps if s is not None]))
+                         if any(s is not None for s in res.warm_steps) else None,
+                         "naive": float(np.median([s for s in res.naive_steps if s is not None]))
+                         if any(s is not None for s in res.naive_steps) else None},
+        "wall_seconds": time.perf_counter() - t_all,
+    }
+    if conv_w and conv_n:
+        out["speedup"] = out["batched_warm"]["intervals_per_s"] / out["plain_naive"]["intervals_per_s"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.converge:
+        run_converge(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

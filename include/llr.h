@@ -111,6 +111,17 @@ int llr_rm_step(llr_handle h, int n_therm, int n_meas, int rm_index, double *a_i
 int llr_rm_step_dev(llr_handle h, int n_therm, int n_meas, int rm_index, const double *a_in,
                     double *a_out, double *dE_mean_out);
 
+/* n_steps Robbins-Monro iterations (Algorithm 1's loop over n) of every
+ * lattice, as replays of one captured CUDA graph (reset of the work queue,
+ * the persistent kernel, and an increment of a device step counter): step k
+ * uses rm_index0 + k in eq. kk21.  a_dev: device double[n_lattices], a^(n)
+ * in, a^(n + n_steps) out; hist_dev: device double[n_steps][n_lattices] of
+ * a after each step, or NULL.  Asynchronous on the handle's stream.  The
+ * graph is captured on the first call and reused while the arguments stay
+ * the same. */
+int llr_rm_run(llr_handle h, int n_therm, int n_meas, int rm_index0, int n_steps, double *a_dev,
+               double *hist_dev);
+
 /* The plain per-interval form of the same iteration, kept as the reference
  * point of the batched form: lattices are processed one after another with
  * one kernel launch per pass, per energy resync and per update (no batching,
@@ -198,6 +209,48 @@ int llr_cv_peak(int n, const double *centres, const double *a, double beta_lo, d
  * approximations for the staples, 0: correctly rounded-class sincosf).
  * Chosen per lattice size by the autotuner; default 256 threads, fast math. */
 int llr_set_kernel_config(llr_handle h, int threads, int fast_math);
+
+/* ---------------------------------------------------------------------------
+ * Learned warm start of the Robbins-Monro iteration (no counterpart in the
+ * paper's algorithm; the paper's justification is that a_k is an intrinsic,
+ * volume independent quantity, Sec. 2.2 eq. kk2 and the appendix eqs.
+ * kkk34-kkk36, and that the initial a only needs to be close, Sec. 2.4).
+ * A multilayer perceptron 3 -> 64 -> 64 -> 64 -> 1 with GELU (erf form)
+ * maps the standardised features (1/V, E/6V, dE/6V), V = L^4 (finite-volume
+ * corrections of a_k are O(1/V), eq. kkk35), to a; FP32 parameters
+ * in one array: W1 (3x64, [in][out]), b1, W2 (64x64), b2, W3 (64x64), b3,
+ * W4 (64x1), b4 (llr_mlp_num_params() floats).  Loss: mean squared error.
+ * All input arrays are host double[n]; calls are synchronous on the stream
+ * given at creation (NULL = legacy default stream).
+ * ------------------------------------------------------------------------ */
+typedef struct llr_mlp *llr_mlp_handle;
+
+/* Create a network with weights ~ N(0, 1/fan_in) from Philox(seed), zero
+ * biases, identity standardisation (mean 0, std 1). */
+int llr_mlp_create(llr_mlp_handle *out, uint64_t seed, void *cuda_stream);
+int llr_mlp_num_params(void);
+/* Copy the parameter array to / from a host float[llr_mlp_num_params()];
+ * setting parameters also resets the Adam moments and step count. */
+int llr_mlp_get_params(llr_mlp_handle h, float *out);
+int llr_mlp_set_params(llr_mlp_handle h, const float *in);
+/* Feature standardisation x = (raw - mean) / std, host double[3] each. */
+int llr_mlp_set_norm(llr_mlp_handle h, const double *mean, const double *std);
+int llr_mlp_get_norm(llr_mlp_handle h, double *mean, double *std);
+/* Predicted slopes a_out[n] for inputs (L, E/6V, dE/6V). */
+int llr_mlp_predict(llr_mlp_handle h, int n, const double *L, const double *e6v,
+                    const double *dE6v, double *a_out);
+/* Gradient of the loss on (inputs, a_target) with respect to every
+ * parameter (grad_out: host float[llr_mlp_num_params()]) and the loss. */
+int llr_mlp_grad(llr_mlp_handle h, int n, const double *L, const double *e6v,
+                 const double *dE6v, const double *a_target, float *grad_out, double *loss_out);
+/* Full-batch Adam (beta1 0.9, beta2 0.999, eps 1e-8) for `epochs` steps at
+ * learning rate lr; standardise != 0 first sets mean/std from these inputs.
+ * loss_out (nullable) gets the loss of the final parameters.  The epoch is
+ * captured once in a CUDA graph and replayed. */
+int llr_mlp_fit(llr_mlp_handle h, int n, const double *L, const double *e6v, const double *dE6v,
+                const double *a_target, int epochs, double lr, int standardise,
+                double *loss_out);
+int llr_mlp_destroy(llr_mlp_handle h);
 
 /* Release everything the handle owns. */
 int llr_destroy(llr_handle h);

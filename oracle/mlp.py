@@ -10,7 +10,8 @@ volumes predicts larger ones; Sec. 2.4 says a good initial a only needs to be
 close to the result.
 
 Definition (both the oracle and the CUDA kernels implement exactly this):
-  features  x = ((1/L, E/6V, dE/6V) - mean) / std   (training-set statistics)
+  features  x = ((1/V, E/6V, dE/6V) - mean) / std   (V = L^4; training-set statistics;
+            1/V because the finite-volume corrections of a_k are O(1/V), eq. kkk35)
   h1 = gelu(x W1 + b1)      W1: 3x64
   h2 = gelu(h1 W2 + b2)     W2: 64x64
   h3 = gelu(h2 W3 + b3)     W3: 64x64
@@ -109,7 +110,7 @@ class Adam:
 
 
 def features(L, e6v, dE6v):
-    return np.stack([1.0 / np.asarray(L, dtype=np.float64), np.asarray(e6v, dtype=np.float64),
+    return np.stack([1.0 / np.asarray(L, dtype=np.float64) ** 4, np.asarray(e6v, dtype=np.float64),
                      np.asarray(dE6v, dtype=np.float64)], axis=1)
 
 

@@ -32,6 +32,12 @@ struct llr_ctx {
     llr::LaunchCfg cfg;
     unsigned *d_sync = nullptr;      // work queue of the persistent kernel: 2 + n words
     int *d_order = nullptr;          // 0 .. n-1 (single-lattice launches point into it)
+    int *d_step = nullptr;           // Robbins-Monro step counter of graph replays
+    // one captured Robbins-Monro step (memset, persistent kernel, step + 1)
+    cudaGraphExec_t rm_graph = nullptr;
+    int g_therm = -1, g_meas = -1, g_index0 = -1;
+    double *g_a = nullptr, *g_hist = nullptr;
+    cudaStream_t capture_stream = nullptr;
 };
 
 namespace {
@@ -194,6 +200,7 @@ int llr_init_lattice(llr_handle *out, const llr_config *cfg, void *cuda_stream)
     LLR_CUDA(cudaMalloc(&h->d_int, sizeof(int) * (size_t)(n + 1)));
     LLR_CUDA(cudaMalloc(&h->d_sync, sizeof(unsigned) * (size_t)(n + 2)));
     LLR_CUDA(cudaMalloc(&h->d_order, sizeof(int) * (size_t)n));
+    LLR_CUDA(cudaMalloc(&h->d_step, sizeof(int)));
     {
         std::vector<int> ord((size_t)n);
         for (int i = 0; i < n; ++i) ord[(size_t)i] = i;
@@ -313,6 +320,51 @@ int llr_rm_step(llr_handle h, int n_therm, int n_meas, int rm_index, double *a_i
     for (int i = 0; i < h->n; ++i)
         if (!std::isfinite(a_inout[i]))
             return fail(LLR_ERR_NUMERIC, "non-finite a for lattice " + std::to_string(i));
+    return LLR_OK;
+}
+
+int llr_rm_run(llr_handle h, int n_therm, int n_meas, int rm_index0, int n_steps, double *a_dev,
+               double *hist_dev)
+{
+    if (int r = check_handle(h)) return r;
+    if (!a_dev || n_therm < 0 || n_meas < 1 || rm_index0 < 0 || n_steps < 0)
+        return fail(LLR_ERR_ARG, "bad arguments");
+    if (!h->rm_graph || h->g_therm != n_therm || h->g_meas != n_meas ||
+        h->g_index0 != rm_index0 || h->g_a != a_dev || h->g_hist != hist_dev) {
+        if (h->rm_graph) cudaGraphExecDestroy(h->rm_graph);
+        h->rm_graph = nullptr;
+        if (!h->capture_stream)
+            LLR_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+        llr::KernelArgs a = base_args(h);
+        a.program = llr::kProgRM;
+        a.n_therm = n_therm;
+        a.n_meas = n_meas;
+        a.measure = 1;
+        a.rm_index = rm_index0;
+        a.a_in = a_dev;
+        a.a_out = a_dev;
+        a.step_dev = h->d_step;
+        a.hist = hist_dev;
+        llr::prime_launch(h->cfg);
+        cudaGraph_t g;
+        LLR_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = llr::launch_llr(a, h->cfg, h->capture_stream);
+        cudaError_t e2 = llr::launch_step_increment(h->d_step, h->capture_stream);
+        cudaError_t e3 = cudaStreamEndCapture(h->capture_stream, &g);
+        LLR_CUDA(e1);
+        LLR_CUDA(e2);
+        LLR_CUDA(e3);
+        cudaError_t e4 = cudaGraphInstantiate(&h->rm_graph, g, 0);
+        cudaGraphDestroy(g);
+        LLR_CUDA(e4);
+        h->g_therm = n_therm;
+        h->g_meas = n_meas;
+        h->g_index0 = rm_index0;
+        h->g_a = a_dev;
+        h->g_hist = hist_dev;
+    }
+    LLR_CUDA(cudaMemsetAsync(h->d_step, 0, sizeof(int), h->stream));
+    for (int k = 0; k < n_steps; ++k) LLR_CUDA(cudaGraphLaunch(h->rm_graph, h->stream));
     return LLR_OK;
 }
 
@@ -495,6 +547,9 @@ int llr_destroy(llr_handle h)
     cudaFree(h->d_links);
     cudaFree(h->d_sync);
     cudaFree(h->d_order);
+    cudaFree(h->d_step);
+    if (h->rm_graph) cudaGraphExecDestroy(h->rm_graph);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     delete h;
     return LLR_OK;
 }

@@ -510,12 +510,15 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v)
 // Robbins-Monro update of the CTA's lattice (thread 0).
 __device__ __noinline__ void rm_update(LatState &st, const KernelArgs &args, int lat)
 {
+    const int step = args.step_dev ? *args.step_dev : 0;
     const double mean = st.n_meas > 0 ? st.sum_dE / st.n_meas : 0.0;
-    const double a_new = st.a + 12.0 * mean / (st.dE * st.dE * (double)(args.rm_index + 1));
+    const double a_new =
+        st.a + 12.0 * mean / (st.dE * st.dE * (double)(args.rm_index + step + 1));
     if (!isfinite(a_new)) st.status = -5;   // LLR_ERR_NUMERIC
     st.a = a_new;
     if (args.a_out) args.a_out[lat] = a_new;
     if (args.mean_out) args.mean_out[lat] = mean;
+    if (args.hist) args.hist[(size_t)step * (size_t)args.n_lat + (size_t)lat] = a_new;
 }
 
 // Resident CTAs per SM the register budget is held to (80 registers at 256 threads).
@@ -774,6 +777,17 @@ cudaError_t launch_t(const KernelArgs &a, cudaStream_t s)
 
 }  // namespace
 
+void prime_launch(const LaunchCfg &cfg)
+{
+    if (cfg.threads == 128) {
+        if (cfg.fast_math) resident_ctas<3, true>(); else resident_ctas<3, false>();
+    } else if (cfg.threads == 512) {
+        if (cfg.fast_math) resident_ctas<15, true>(); else resident_ctas<15, false>();
+    } else {
+        if (cfg.fast_math) resident_ctas<7, true>(); else resident_ctas<7, false>();
+    }
+}
+
 cudaError_t launch_llr(const KernelArgs &a, const LaunchCfg &cfg, cudaStream_t s)
 {
     if (a.n_lat <= 0) return cudaSuccess;
@@ -782,6 +796,17 @@ cudaError_t launch_llr(const KernelArgs &a, const LaunchCfg &cfg, cudaStream_t s
     if (cfg.threads == 512)
         return cfg.fast_math ? launch_t<15, true>(a, s) : launch_t<15, false>(a, s);
     return cfg.fast_math ? launch_t<7, true>(a, s) : launch_t<7, false>(a, s);
+}
+
+__global__ void step_increment_kernel(int *step)
+{
+    *step += 1;
+}
+
+cudaError_t launch_step_increment(int *step, cudaStream_t s)
+{
+    step_increment_kernel<<<1, 1, 0, s>>>(step);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_hot_start(LatState *lats, float *theta, int n_lat, int max_half,

@@ -44,12 +44,22 @@ struct KernelArgs {
     // work queue (device): [0] item counter, [1] error word, [2 ..] sweeps done per slot
     unsigned *sync;
     unsigned long long wait_limit_ns;   // bounded wait for a lattice's previous sweep
+    // graph replays: the Robbins-Monro step number lives in device memory
+    const int *step_dev;  // nullable: rm_index += *step_dev, history row *step_dev
+    double *hist;         // nullable: hist[step * n_lat + lattice] = new a
 };
+
+// *step += 1 (the last node of a captured Robbins-Monro step).
+cudaError_t launch_step_increment(int *step, cudaStream_t s);
 
 struct LaunchCfg {
     int threads = 256;    // 128, 256 or 512: one consumer warp, the rest producers
     bool fast_math = true;
 };
+
+// Query (and cache) the resident-CTA count of a kernel variant; call before a
+// stream capture so the capture itself makes no occupancy queries.
+void prime_launch(const LaunchCfg &cfg);
 
 // Reset the work queue and launch the persistent kernel (stream ordered).
 cudaError_t launch_llr(const KernelArgs &a, const LaunchCfg &cfg, cudaStream_t s);

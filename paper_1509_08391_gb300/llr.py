@@ -23,11 +23,14 @@ LLR_ERR_NUMERIC = -5
 
 # Every entry point declared in include/llr.h.
 EXPORTS = [
-    "llr_init_lattice", "llr_approach", "llr_sweep", "llr_pass", "llr_rm_step", "llr_rm_step_dev",
+    "llr_init_lattice", "llr_approach", "llr_sweep", "llr_pass", "llr_rm_step", "llr_rm_run", "llr_rm_step_dev",
     "llr_rm_step_plain", "llr_energy", "llr_tracked_energy", "llr_get_links", "llr_set_links",
     "llr_get_sweep_counter", "llr_set_sweep_counter", "llr_stats", "llr_status",
     "llr_reconstruct_lnrho", "llr_observables", "llr_cv_peak", "llr_set_kernel_config",
     "llr_destroy", "llr_last_error", "llr_observables_noalloc",
+    "llr_mlp_create", "llr_mlp_num_params", "llr_mlp_get_params", "llr_mlp_set_params",
+    "llr_mlp_set_norm", "llr_mlp_get_norm", "llr_mlp_predict", "llr_mlp_grad", "llr_mlp_fit",
+    "llr_mlp_destroy",
 ]
 NOALLOC_MAX_CENTRES = 65536
 
@@ -74,6 +77,7 @@ def load(path: str = LIB_PATH):
         "llr_pass": [P, I, P, I],
         "llr_rm_step": [P, I, I, I, P, P],
         "llr_rm_step_dev": [P, I, I, I, P, P, P],
+        "llr_rm_run": [P, I, I, I, I, P, P],
         "llr_rm_step_plain": [P, I, I, I, P, P],
         "llr_energy": [P, P],
         "llr_tracked_energy": [P, P],
@@ -89,6 +93,16 @@ def load(path: str = LIB_PATH):
         "llr_set_kernel_config": [P, I, I],
         "llr_destroy": [P],
         "llr_observables_noalloc": [I, P, P, I, P, P, P, P, P],
+        "llr_mlp_create": [ctypes.POINTER(P), ctypes.c_uint64, P],
+        "llr_mlp_num_params": [],
+        "llr_mlp_get_params": [P, P],
+        "llr_mlp_set_params": [P, P],
+        "llr_mlp_set_norm": [P, P, P],
+        "llr_mlp_get_norm": [P, P, P],
+        "llr_mlp_predict": [P, I, P, P, P, P],
+        "llr_mlp_grad": [P, I, P, P, P, P, P, P],
+        "llr_mlp_fit": [P, I, P, P, P, P, I, D, I, P],
+        "llr_mlp_destroy": [P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -199,6 +213,11 @@ class Batch:
         _check(load().llr_rm_step_dev(self._h, int(n_therm), int(n_meas), int(rm_index),
                                       _dev_ptr(a_in), _dev_ptr(a_out), _dev_ptr(mean_out)))
 
+    def rm_run(self, a_dev, n_therm, n_meas, rm_index0, n_steps, hist_dev=None):
+        """n_steps graph-replayed Robbins-Monro iterations on device buffers."""
+        _check(load().llr_rm_run(self._h, int(n_therm), int(n_meas), int(rm_index0),
+                                 int(n_steps), _dev_ptr(a_dev), _dev_ptr(hist_dev)))
+
     def rm_step_plain(self, a, n_therm, n_meas, rm_index):
         a = np.ascontiguousarray(np.broadcast_to(a, (self.n,)), dtype=np.float64).copy()
         mean = np.zeros(self.n)
@@ -283,3 +302,81 @@ def observables_noalloc(centres_dev, a_dev, beta_dev, lnZ_dev, E_dev, E2_dev, st
                                           int(nb), _dev_ptr(beta_dev), _dev_ptr(lnZ_dev),
                                           _dev_ptr(E_dev), _dev_ptr(E2_dev),
                                           ctypes.c_void_p(stream) if stream else None))
+
+
+class MLP:
+    """The warm-start network (llr_mlp_* entry points)."""
+
+    def __init__(self, seed=1, stream=None):
+        lib = load()
+        h = ctypes.c_void_p()
+        code = lib.llr_mlp_create(ctypes.byref(h), int(seed) & (2 ** 64 - 1),
+                                  ctypes.c_void_p(stream) if stream else None)
+        self._h = h
+        _check(code)
+        self.n_params = lib.llr_mlp_num_params()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().llr_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def _in(L, e, d):
+        return [np.ascontiguousarray(x, dtype=np.float64) for x in (L, e, d)]
+
+    def get_params(self):
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().llr_mlp_get_params(self._h, _ptr(out)))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        _check(load().llr_mlp_set_params(self._h, _ptr(p)))
+
+    def set_norm(self, mean, std):
+        m = np.ascontiguousarray(mean, dtype=np.float64)
+        s = np.ascontiguousarray(std, dtype=np.float64)
+        _check(load().llr_mlp_set_norm(self._h, _ptr(m), _ptr(s)))
+
+    def get_norm(self):
+        m, s = np.zeros(3), np.zeros(3)
+        _check(load().llr_mlp_get_norm(self._h, _ptr(m), _ptr(s)))
+        return m, s
+
+    def predict(self, L, e6v, dE6v):
+        L, e, d = self._in(L, e6v, dE6v)
+        out = np.zeros(L.size)
+        _check(load().llr_mlp_predict(self._h, L.size, _ptr(L), _ptr(e), _ptr(d), _ptr(out)))
+        return out
+
+    def grad(self, L, e6v, dE6v, target):
+        L, e, d = self._in(L, e6v, dE6v)
+        t = np.ascontiguousarray(target, dtype=np.float64)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(load().llr_mlp_grad(self._h, L.size, _ptr(L), _ptr(e), _ptr(d), _ptr(t), _ptr(g),
+                                   ctypes.byref(loss)))
+        return g, loss.value
+
+    def fit(self, L, e6v, dE6v, target, epochs, lr=1e-3, standardise=True):
+        L, e, d = self._in(L, e6v, dE6v)
+        t = np.ascontiguousarray(target, dtype=np.float64)
+        loss = ctypes.c_double(0.0)
+        _check(load().llr_mlp_fit(self._h, L.size, _ptr(L), _ptr(e), _ptr(d), _ptr(t),
+                                  int(epochs), float(lr), 1 if standardise else 0,
+                                  ctypes.byref(loss)))
+        return loss.value
