@@ -41,7 +41,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n-therm", type=int, default=2)
     p.add_argument("--n-meas", type=int, default=8)
-    p.add_argument("--threads", type=int, default=256)
+    p.add_argument("--threads", type=int, default=0,
+                   help="threads per CTA (128/256/512); 0 = autotuned")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--intervals", type=int, default=256)
@@ -118,6 +119,7 @@ def config_dict(args, w, world):
             "sweeps_per_step": args.n_therm + args.n_meas, "n_therm": args.n_therm,
             "n_meas": args.n_meas, "accept_block": w.block,
             "parallelism": "dp%d (independent lattices, no collective)" % world,
+            "threads_per_cta": getattr(args, "threads_used", args.threads),
             "l2": "inputs larger than L2 (5.2 GB of links per GPU)"}
 
 
@@ -189,9 +191,15 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
 
     w = workload(args, rank)
+    threads = args.threads
+    if threads == 0:
+        from paper_1509_08391_gb300 import autotune
+        threads = autotune.tune(w)
     stream = torch.cuda.Stream(device=dev)
     b = llr.Batch.from_workload(w, stream=stream.cuda_stream, max_approach=1000)
-    b.set_kernel_config(args.threads, True)
+    b.set_kernel_config(threads, True)
+    b.stats(reset=True)
+    args.threads_used = threads
     n = w.n_lattices
     upd_per_step = n * (args.n_therm + args.n_meas) * (1 + w.n_or) * 4 * 20 ** 4
 

@@ -43,9 +43,10 @@
  *      the indicator of eq. kk7; outside it only lets E move towards the
  *      window (used while approaching the window from a hot start).
  *   R3 heat-bath proposal: von Mises variate by Best & Fisher (1979).
- *   R4 random numbers: Philox4x32-10 (Salmon et al., SC'11), one call per
- *      sampler attempt, keyed by (seed, interval, replica), counter
- *      (link, sweep, tag, attempt).
+ *   R4 random numbers: Philox4x32-10 (Salmon et al., SC'11), keyed by
+ *      (seed, interval, replica), counter (link, sweep, tag, attempt / 2):
+ *      one call serves two sampler attempts (words 0-1 and 2-3; the sign of
+ *      X is the lowest bit of the attempt's first word).
  *   R5 approach phase: from a hot start, heat-bath at a = -beta_up (E below
  *      the window) or a = -beta_dn (E above) with the dist rule, until the
  *      energy lies in the window at the end of a composite sweep.
@@ -349,6 +350,9 @@ void orc_lat_hot_start(orc_lat *t)
 }
 
 /* Best & Fisher (1979) von Mises sampler for density ~ exp(kappa cos X).
+ * Attempt t uses Philox call t/2 (counter word 3): words 0, 1 for even t and
+ * words 2, 3 for odd t give u1 and u2, and the lowest bit of the attempt's
+ * first word (not used by its uniform) gives the sign of X.
  * Returns the number of attempts used, or -1 if the attempt cap was hit. */
 int orc_vonmises(double kappa, const uint32_t key[2], uint32_t c0, uint32_t c1, uint32_t c2,
                  double *X)
@@ -363,15 +367,19 @@ int orc_vonmises(double kappa, const uint32_t key[2], uint32_t c0, uint32_t c1, 
     double tau = 1.0 + sqrt(1.0 + 4.0 * k * k);
     double rho = (tau - sqrt(2.0 * tau)) / (2.0 * k);
     double r = (1.0 + rho * rho) / (2.0 * rho);
+    uint32_t w[4];
     for (uint32_t att = 0; att < SAMPLER_MAX_ATTEMPTS; ++att) {
-        uint32_t ctr[4] = {c0, c1, c2, att}, w[4];
-        orc_philox4x32_10(ctr, key, w);
-        double u1 = orc_uniform(w[0]), u2 = orc_uniform(w[1]), u3 = orc_uniform(w[2]);
+        if ((att & 1u) == 0u) {
+            uint32_t ctr[4] = {c0, c1, c2, att >> 1};
+            orc_philox4x32_10(ctr, key, w);
+        }
+        uint32_t wa = w[2 * (att & 1u)], wb = w[2 * (att & 1u) + 1];
+        double u1 = orc_uniform(wa), u2 = orc_uniform(wb);
         double z = cos(M_PI * u1);
         double f = (1.0 + r * z) / (r + z);
         double c = k * (r - f);
         if (c * (2.0 - c) - u2 > 0.0 || log(c / u2) + 1.0 - c >= 0.0) {
-            double x = (u3 > 0.5 ? 1.0 : -1.0) * acos(f);
+            double x = (wa & 1u ? 1.0 : -1.0) * acos(f);
             if (kappa < 0.0) x = wrap_angle(x + M_PI);
             *X = x;
             return (int)att + 1;

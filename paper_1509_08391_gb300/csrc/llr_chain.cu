@@ -51,12 +51,15 @@ constexpr int kStages = 4;
 // ---------------------------------------------------------------------------
 // Best & Fisher (1979) von Mises sampler, density ~ exp(kappa cos X).
 // tau = 1 + sqrt(1 + 4 k^2), rho = (tau - sqrt(2 tau)) / (2 k) (rewritten
-// without cancellation), r = (1 + rho^2) / (2 rho).  Per attempt:
+// without cancellation), r = (1 + rho^2) / (2 rho).  Attempt t uses Philox
+// call t/2 (counter word 3), words 0-1 (t even) or 2-3 (t odd) as u1, u2,
+// and the lowest bit of the first of them as the sign of X:
 // z = cos(pi u1), f = (1 + r z) / (r + z), c = k (r - f); accept if
-// c (2 - c) > u2 or ln(c / u2) + 1 - c >= 0; X = +-acos(f) by u3.  acos(f) is
-// evaluated as 2 asin(sqrt((1-f)/2)) or pi - 2 asin(sqrt((1+f)/2)) with
-// 1 -+ f formed without cancellation, so small and near-pi angles keep
-// full float precision.
+// c (2 - c) > u2 or ln(c / u2) + 1 - c >= 0.  The accept test runs on fast
+// hardware approximations (it only decides which attempt is taken); the
+// accepted variate is then evaluated accurately: acos(f) as
+// 2 asin(sqrt((1-f)/2)) or pi - 2 asin(sqrt((1+f)/2)) with 1 -+ f formed
+// without cancellation, so small and near-pi angles keep full precision.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool von_mises(float kappa, uint32_t c0, uint32_t c1, uint32_t c2,
                                           uint32_t k0, uint32_t k1, float &X, float &cX)
@@ -71,36 +74,53 @@ __device__ __forceinline__ bool von_mises(float kappa, uint32_t c0, uint32_t c1,
     const float k = fabsf(kappa);
     const float sq = sqrtf(fmaf(4.0f * k, k, 1.0f));
     const float tau = 1.0f + sq;
-    const float rho = 2.0f * k * tau / ((sq + 1.0f) * (tau + sqrtf(2.0f * tau)));
-    const float r = (1.0f + rho * rho) / (2.0f * rho);
+    const float rho = __fdividef(2.0f * k * tau, (sq + 1.0f) * (tau + sqrtf(2.0f * tau)));
+    const float r = __fdividef(1.0f + rho * rho, 2.0f * rho);
     const float omr = 1.0f - rho;
-    const float rm1 = omr * omr / (2.0f * rho);   // r - 1
-    for (int att = 0; att < kSamplerMaxAttempts; ++att) {
-        const U4 w = philox4x32_10(c0, c1, c2, (uint32_t)att, k0, k1);
-        const float u1 = u01(w.x), u2 = u01(w.y), u3 = u01(w.z);
-        const float z = cospif(u1);
-        const float den = r + z;
-        const float f = (1.0f + r * z) / den;
-        const float c = k * (rm1 + (1.0f - f));
-        if (c * (2.0f - c) - u2 > 0.0f || logf(c / u2) + 1.0f - c >= 0.0f) {
-            float mag;
-            if (f >= 0.0f) {
-                const float sh = sinpif(0.5f * u1);
-                const float g = rm1 * 2.0f * sh * sh / den;            // 1 - f
-                mag = 2.0f * asinf(fminf(sqrtf(0.5f * g), 1.0f));
-            } else {
-                const float ch = cospif(0.5f * u1);
-                const float hp = (r + 1.0f) * 2.0f * ch * ch / den;    // 1 + f
-                mag = kPi - 2.0f * asinf(fminf(sqrtf(0.5f * hp), 1.0f));
+    const float rm1 = __fdividef(omr * omr, 2.0f * rho);   // r - 1
+    // find the first accepted attempt (cheap test only, so lanes that accept
+    // at different attempts diverge over as little code as possible) ...
+    bool found = false;
+    uint32_t w_acc = 0u;
+    for (int pair = 0; pair < kSamplerMaxAttempts / 2 && !found; ++pair) {
+        const U4 w = philox4x32_10(c0, c1, c2, (uint32_t)pair, k0, k1);
+#pragma unroll
+        for (int half_ = 0; half_ < 2; ++half_) {
+            const uint32_t wa = half_ ? w.z : w.x, wb = half_ ? w.w : w.y;
+            const float u1 = u01(wa), u2 = u01(wb);
+            const float z = __cosf(kPi * u1);
+            const float f = __fdividef(1.0f + r * z, r + z);
+            const float c = k * (rm1 + (1.0f - f));
+            if (!found &&
+                (c * (2.0f - c) - u2 > 0.0f || __logf(c) - __logf(u2) + 1.0f - c >= 0.0f)) {
+                found = true;
+                w_acc = wa;
             }
-            float x = u3 > 0.5f ? mag : -mag;
-            if (kappa < 0.0f) x = wrap_angle(x + kPi);
-            X = x;
-            cX = kappa < 0.0f ? -f : f;
-            return true;
         }
     }
-    return false;
+    if (!found) return false;
+    // ... then evaluate the accepted variate once, accurately
+    const float u1 = u01(w_acc);
+    const float z = cospif(u1);
+    const float den = r + z;
+    const float f = (1.0f + r * z) / den;
+    float mag, fa;
+    if (f >= 0.0f) {
+        const float sh = sinpif(0.5f * u1);
+        const float g = rm1 * 2.0f * sh * sh / den;            // 1 - f
+        mag = 2.0f * asinf(fminf(sqrtf(0.5f * g), 1.0f));
+        fa = 1.0f - g;
+    } else {
+        const float ch = cospif(0.5f * u1);
+        const float hp = (r + 1.0f) * 2.0f * ch * ch / den;    // 1 + f
+        mag = kPi - 2.0f * asinf(fminf(sqrtf(0.5f * hp), 1.0f));
+        fa = hp - 1.0f;
+    }
+    float x = (w_acc & 1u) ? mag : -mag;
+    if (kappa < 0.0f) x = wrap_angle(x + kPi);
+    X = x;
+    cX = kappa < 0.0f ? -fa : fa;
+    return true;
 }
 
 template <bool FAST>
@@ -521,9 +541,10 @@ __device__ __noinline__ void rm_update(LatState &st, const KernelArgs &args, int
     if (args.hist) args.hist[(size_t)step * (size_t)args.n_lat + (size_t)lat] = a_new;
 }
 
-// Resident CTAs per SM the register budget is held to (80 registers at 256 threads).
+// Resident CTAs per SM the register budget is held to: 128 threads x 8 and
+// 512 threads x 2 (64 registers), 256 threads x 3 (80 registers).
 template <int NWP>
-constexpr int min_ctas() { return NWP == 3 ? 6 : (NWP == 7 ? 3 : 1); }
+constexpr int min_ctas() { return NWP == 3 ? 8 : (NWP == 7 ? 3 : 2); }
 
 template <int NWP, bool FAST>
 __global__ void __launch_bounds__((NWP + 1) * 32, min_ctas<NWP>()) llr_kernel(KernelArgs args)
