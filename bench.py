@@ -112,6 +112,21 @@ def workload(args, rank):
     return w
 
 
+def aggregate(units_per_rank, seconds, dist=None, device=None):
+    """Whole-job throughput: units of all ranks over the slowest rank's time
+    (max over ranks, the barrier-bracketed timing of the benchmark contract)."""
+    total, t = float(units_per_rank), float(seconds)
+    if dist is not None and dist.is_initialized():
+        import torch
+        v = torch.tensor([total, t], dtype=torch.float64, device=device)
+        tot = v[:1].clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        mx = v[1:].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        total, t = float(tot.item()), float(mx.item())
+    return total / t, t
+
+
 def config_dict(args, w, world):
     return {"workload": w.name, "L": 20, "lattices_per_gpu": w.n_lattices,
             "intervals": args.intervals, "replicas": 8, "dE": 12.0,
@@ -229,12 +244,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    per_launch_ms = ms / args.steps
-    value = world * upd_per_step * args.steps / (ms / 1e3)
+    value, secs = aggregate(upd_per_step * args.steps, ms / 1e3, dist, dev)
+    per_launch_ms = 1e3 * secs / args.steps
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -258,11 +269,8 @@ def run_ours(args, rank, world, local_rank):
             if code != 0:
                 raise RuntimeError(lib.llr_last_error().decode())
         dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * upd_per_step * ke / dt, "unit": METRIC,
+        e2e_value, _ = aggregate(upd_per_step * ke, dt, dist, dev)
+        e2e = {"value": e2e_value, "unit": METRIC,
                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 16 * n,
                "steps": ke}
 

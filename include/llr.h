@@ -30,6 +30,7 @@
 #ifndef LLR_H
 #define LLR_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -251,6 +252,22 @@ int llr_mlp_fit(llr_mlp_handle h, int n, const double *L, const double *e6v, con
                 const double *a_target, int epochs, double lr, int standardise,
                 double *loss_out);
 int llr_mlp_destroy(llr_mlp_handle h);
+
+/* Upper bound on how long a work item of the batched kernel waits for the
+ * previous sweep of its lattice (default 20 s).  When it runs out the item
+ * is skipped, the lattice keeps its state and llr_status / the synchronous
+ * calls return LLR_ERR_TIMEOUT; the CUDA context stays usable. */
+int llr_set_wait_limit(llr_handle h, unsigned long long ns);
+
+/* Checkpoint / resume.  The whole chain state of every lattice (link angles,
+ * tracked energies, sweep counters, slopes, statistics) fits in
+ * llr_state_bytes(h) bytes; llr_save_state copies it to the host buffer
+ * `out`, llr_load_state copies it back into a handle created with the same
+ * configuration (checked: LLR_ERR_ARG otherwise).  Random numbers are keyed
+ * by the sweep counter, so a resumed run continues bit-identically. */
+size_t llr_state_bytes(llr_handle h);
+int llr_save_state(llr_handle h, void *out);
+int llr_load_state(llr_handle h, const void *in);
 
 /* Release everything the handle owns. */
 int llr_destroy(llr_handle h);

@@ -30,6 +30,7 @@ struct llr_ctx {
     int n_or = 4, block = 1;
     double beta_up = 1.5, beta_dn = 0.5;
     llr::LaunchCfg cfg;
+    unsigned long long wait_limit_ns = 20000000000ull;
     unsigned *d_sync = nullptr;      // work queue of the persistent kernel: 2 + n words
     int *d_order = nullptr;          // 0 .. n-1 (single-lattice launches point into it)
     int *d_step = nullptr;           // Robbins-Monro step counter of graph replays
@@ -62,9 +63,6 @@ bool pow2_block(int b)
     return b >= 1 && b <= 32 && (b & (b - 1)) == 0;
 }
 
-// A lattice's previous sweep is never waited for longer than this.
-constexpr unsigned long long kWaitLimitNs = 20000000000ull;
-
 llr::KernelArgs base_args(llr_handle h)
 {
     llr::KernelArgs a;
@@ -78,7 +76,7 @@ llr::KernelArgs base_args(llr_handle h)
     a.beta_dn = h->beta_dn;
     a.class_mask = 0xFF;
     a.sync = h->d_sync;
-    a.wait_limit_ns = kWaitLimitNs;
+    a.wait_limit_ns = h->wait_limit_ns;
     return a;
 }
 
@@ -531,6 +529,52 @@ int llr_set_kernel_config(llr_handle h, int threads, int fast_math)
         return fail(LLR_ERR_ARG, "threads must be 128, 256 or 512");
     h->cfg.threads = threads;
     h->cfg.fast_math = fast_math != 0;
+    return LLR_OK;
+}
+
+int llr_set_wait_limit(llr_handle h, unsigned long long ns)
+{
+    if (int r = check_handle(h)) return r;
+    h->wait_limit_ns = ns;
+    return LLR_OK;
+}
+
+size_t llr_state_bytes(llr_handle h)
+{
+    if (!h) return 0;
+    return sizeof(LatState) * (size_t)h->n + sizeof(float) * h->n_floats;
+}
+
+int llr_save_state(llr_handle h, void *out)
+{
+    if (int r = check_handle(h)) return r;
+    if (!out) return fail(LLR_ERR_ARG, "null buffer");
+    char *p = (char *)out;
+    LLR_CUDA(cudaMemcpyAsync(p, h->d_lat, sizeof(LatState) * (size_t)h->n, cudaMemcpyDeviceToHost,
+                             h->stream));
+    LLR_CUDA(cudaMemcpyAsync(p + sizeof(LatState) * (size_t)h->n, h->d_theta,
+                             sizeof(float) * h->n_floats, cudaMemcpyDeviceToHost, h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    return LLR_OK;
+}
+
+int llr_load_state(llr_handle h, const void *in)
+{
+    if (int r = check_handle(h)) return r;
+    if (!in) return fail(LLR_ERR_ARG, "null buffer");
+    const LatState *st = (const LatState *)in;
+    for (int i = 0; i < h->n; ++i) {
+        const LatState &a = st[i], &b = h->h_lat[(size_t)i];
+        if (a.L != b.L || a.half != b.half || a.off != b.off || a.key0 != b.key0 ||
+            a.key1 != b.key1 || a.lo_fx != b.lo_fx || a.hi_fx != b.hi_fx)
+            return fail(LLR_ERR_ARG, "state of lattice " + std::to_string(i) +
+                                         " was saved from a different configuration");
+    }
+    LLR_CUDA(cudaMemcpyAsync(h->d_lat, in, sizeof(LatState) * (size_t)h->n, cudaMemcpyHostToDevice,
+                             h->stream));
+    LLR_CUDA(cudaMemcpyAsync(h->d_theta, (const char *)in + sizeof(LatState) * (size_t)h->n,
+                             sizeof(float) * h->n_floats, cudaMemcpyHostToDevice, h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
     return LLR_OK;
 }
 

@@ -30,7 +30,8 @@ EXPORTS = [
     "llr_destroy", "llr_last_error", "llr_observables_noalloc",
     "llr_mlp_create", "llr_mlp_num_params", "llr_mlp_get_params", "llr_mlp_set_params",
     "llr_mlp_set_norm", "llr_mlp_get_norm", "llr_mlp_predict", "llr_mlp_grad", "llr_mlp_fit",
-    "llr_mlp_destroy",
+    "llr_mlp_destroy", "llr_set_wait_limit", "llr_state_bytes", "llr_save_state",
+    "llr_load_state",
 ]
 NOALLOC_MAX_CENTRES = 65536
 
@@ -103,11 +104,16 @@ def load(path: str = LIB_PATH):
         "llr_mlp_grad": [P, I, P, P, P, P, P, P],
         "llr_mlp_fit": [P, I, P, P, P, P, I, D, I, P],
         "llr_mlp_destroy": [P],
+        "llr_set_wait_limit": [P, ctypes.c_ulonglong],
+        "llr_save_state": [P, P],
+        "llr_load_state": [P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = I
+    L.llr_state_bytes.argtypes = [P]
+    L.llr_state_bytes.restype = ctypes.c_size_t
     L.llr_last_error.argtypes = []
     L.llr_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -264,6 +270,20 @@ class Batch:
         out = np.zeros(self.n, dtype=np.int32)
         _check(load().llr_status(self._h, _ptr(out)))
         return out
+
+    def set_wait_limit(self, ns):
+        _check(load().llr_set_wait_limit(self._h, int(ns)))
+
+    def save_state(self):
+        """The chain state of every lattice as bytes (checkpoint)."""
+        buf = np.zeros(load().llr_state_bytes(self._h), dtype=np.uint8)
+        _check(load().llr_save_state(self._h, _ptr(buf)))
+        return buf.tobytes()
+
+    def load_state(self, blob):
+        buf = np.frombuffer(blob, dtype=np.uint8).copy()
+        assert buf.size == load().llr_state_bytes(self._h)
+        _check(load().llr_load_state(self._h, _ptr(buf)))
 
 
 def reconstruct_lnrho(centres, a):
