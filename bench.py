@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--target-intervals", type=int, default=32)
     p.add_argument("--target-replicas", type=int, default=4)
     p.add_argument("--n-rm", type=int, default=150)
+    p.add_argument("--phases", action="store_true",
+                   help="profiling driver: one overrelaxation pass, one heat-bath pass and one "
+                        "composite sweep of 512 lattices of the workload (for ncu)")
     return p.parse_args()
 
 
@@ -193,6 +196,23 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def kernel_traffic(lattice_sweeps):
+    """DRAM bytes (read + write) of one launch of the sweep kernel, from the ncu
+    counters committed under profiles/: bytes per lattice-sweep of the captured
+    case times the lattice-sweeps of this launch (the traffic grows in
+    proportion to them).  None when the kernel source has changed since the
+    capture."""
+    import hashlib
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "llr_kernel_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_1509_08391_gb300", "csrc", "llr_chain.cu"), "rb").read()
+    except (OSError, ValueError):
+        return None
+    if prof.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return float(prof["dram_bytes_per_lattice_sweep"]) * lattice_sweeps
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -294,13 +314,7 @@ def run_ours(args, rank, world, local_rank):
     except Exception:
         pass
     ach_hbm = BYTES_PER_UPDATE * upd_per_launch / (per_launch_ms / 1e3) / 1e9
-    traffic = None
-    try:
-        prof = json.load(open(os.path.join(ROOT, "profiles", "chain_kernel_traffic.json")))
-        if prof.get("sweeps_per_step") == args.n_therm + args.n_meas and prof.get("valid"):
-            traffic = prof["dram_bytes_per_launch"]
-    except Exception:
-        pass
+    traffic = kernel_traffic(n * (args.n_therm + args.n_meas))
     out = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_launch_ms, "higher_is_better": True,
@@ -393,8 +407,31 @@ def run_converge(args):
     print(json.dumps(out), flush=True)
 
 
+def run_phases(args):
+    """One launch per pass kind on 512 lattices of the benchmark workload, so an
+    ncu capture (-k regex:llr_kernel) sees: resync, approach, overrelaxation
+    pass, heat-bath pass, composite sweep."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1509_08391_gb300 import build as bld
+    bld.build()
+    from paper_1509_08391_gb300 import llr, workloads
+    w = workloads.subset(workloads.l20_critical(), range(512))
+    with llr.Batch.from_workload(w, max_approach=1000) as b:
+        b.set_kernel_config(args.threads or 256, True)
+        a = np.full(w.n_lattices, -1.01)
+        b.single_pass(1, a)
+        b.single_pass(0, a)
+        b.sweep(a, 1)
+        torch.cuda.synchronize()
+    print(json.dumps({"phases": "done", "lattices": w.n_lattices}))
+
+
 def main():
     args = parse()
+    if args.phases:
+        run_phases(args)
+        return
     if args.converge:
         run_converge(args)
         return

@@ -29,15 +29,20 @@
  *   R1 update scheme: the paper names only "an importance sampling
  *      algorithm for one sweep" (Algorithm 1) and mentions heat-bath and
  *      Metropolis.  A composite sweep here is one heat-bath pass followed by
- *      n_or overrelaxation passes.  A pass visits the 2*d checkerboard
- *      classes (direction mu, site parity p) in the order mu = 0..d-1,
- *      p = 0,1; links of one class share no plaquette.
+ *      n_or overrelaxation passes.  A heat-bath pass visits the 2*d
+ *      checkerboard classes (direction mu, site parity p) in the order
+ *      mu = 0..d-1, p = 0,1, each over the whole lattice; an overrelaxation
+ *      pass walks the slabs of the last coordinate and, within a slab, the
+ *      classes in the same order.  Links of one class share no plaquette, so
+ *      each group (a class, or a class within a slab) is one set of
+ *      independent proposals.
  *   R2 window restriction (Sec. 2.4 allows imposing it after the proposal):
  *      within a class every link draws an independent proposal from its
  *      unrestricted conditional distribution (heat-bath at weight exp(-aE),
  *      or the overrelaxation reflection); the proposals are then accepted
  *      or rejected in ascending site order, in blocks of B consecutive
- *      links, by the Metropolis rule for the restricted measure: a block is
+ *      links starting at the group's first link, by the Metropolis rule for
+ *      the restricted measure: a block is
  *      accepted iff dist(E + dE_block) <= dist(E), where dist is the distance
  *      of E from the window (0 inside).  Inside the window this is exactly
  *      the indicator of eq. kk7; outside it only lets E move towards the
@@ -395,15 +400,29 @@ static double dist_to_window(double E, double lo, double hi)
     return 0.0;
 }
 
-/* Update one checkerboard class.  mode 0: heat-bath at parameter a with
- * Philox tag `tag`; mode 1: overrelaxation. */
-static void class_pass(orc_lat *t, int cls, int mode, double a, uint32_t tag)
+/* Index range of class cls's links (in update order) that lie in slab sl,
+ * the sites whose last coordinate x_{d-1} equals sl.  The class lists are in
+ * ascending site order, which is slab-major. */
+static void slab_range(const orc_geom *g, int cls, int sl, int *b, int *e)
+{
+    int c0 = g->class_start[cls], c1 = g->class_start[cls + 1];
+    int per_slab = g->nsite / g->dims[g->d - 1];
+    int i = c0;
+    while (i < c1 && (g->class_links[i] % g->nsite) / per_slab < sl) ++i;
+    *b = i;
+    while (i < c1 && (g->class_links[i] % g->nsite) / per_slab == sl) ++i;
+    *e = i;
+}
+
+/* Update the links class_links[c0 .. c1) of one class.  mode 0: heat-bath at
+ * parameter a with Philox tag `tag`; mode 1: overrelaxation.  Window-accept
+ * blocks of B links start at c0. */
+static void group_update(orc_lat *t, int c0, int c1, int mode, double a, uint32_t tag)
 {
     const orc_geom *g = t->g;
     double phi[8];
     double lo = t->E_lo, hi = t->E_lo + t->dE;
-    int c0 = g->class_start[cls], c1 = g->class_start[cls + 1];
-    /* proposals: independent for all links of the class */
+    /* proposals: independent for all links of the group */
     for (int i = c0; i < c1; ++i) {
         int l = g->class_links[i];
         int n = staples(t, l, phi);
@@ -422,7 +441,7 @@ static void class_pass(orc_lat *t, int cls, int mode, double a, uint32_t tag)
         t->prop[l] = thn;
         t->dEl[l] = local_energy(n, phi, thn) - local_energy(n, phi, th);
     }
-    /* sequential Metropolis accept in blocks of B links, ascending order */
+    /* sequential Metropolis accept in blocks of B links, update order */
     for (int b0 = c0; b0 < c1; b0 += t->block) {
         int b1 = b0 + t->block < c1 ? b0 + t->block : c1;
         double d = 0.0;
@@ -435,6 +454,27 @@ static void class_pass(orc_lat *t, int cls, int mode, double a, uint32_t tag)
         if (mode == 0) { t->hb_tot += b1 - b0; if (acc) t->hb_acc += b1 - b0; }
         else           { t->or_tot += b1 - b0; if (acc) t->or_acc += b1 - b0; }
     }
+}
+
+/* The groups of one class in update order: a heat-bath pass takes the whole
+ * class as one group, an overrelaxation pass one group per slab. */
+static int class_groups(const orc_geom *g, int cls, int mode, int *b, int *e)
+{
+    if (mode == 0) {
+        b[0] = g->class_start[cls];
+        e[0] = g->class_start[cls + 1];
+        return 1;
+    }
+    int ns = g->dims[g->d - 1];
+    for (int sl = 0; sl < ns; ++sl) slab_range(g, cls, sl, &b[sl], &e[sl]);
+    return ns;
+}
+
+static void class_pass(orc_lat *t, int cls, int mode, double a, uint32_t tag)
+{
+    int b[64], e[64];
+    int n = class_groups(t->g, cls, mode, b, e);
+    for (int k = 0; k < n; ++k) group_update(t, b[k], e[k], mode, a, tag);
 }
 
 /* The same class update as class_pass, recording for every link of the
@@ -452,26 +492,43 @@ int orc_lat_class_trace(orc_lat *t, int cls, int mode, double a, double *th_old,
     /* replay the decisions of class_pass on a copy of the energy */
     double E = t->E;
     class_pass(t, cls, mode, a, TAG_HB);
-    for (int b0 = c0; b0 < c1; b0 += t->block) {
-        int b1 = b0 + t->block < c1 ? b0 + t->block : c1;
-        double d = 0.0;
-        for (int i = b0; i < b1; ++i) d += t->dEl[g->class_links[i]];
-        int acc = dist_to_window(E + d, lo, hi) <= dist_to_window(E, lo, hi);
-        for (int i = b0; i < b1; ++i) {
-            th_prop[i - c0] = t->prop[g->class_links[i]];
-            E_before[i - c0] = E;
-            dE_block[i - c0] = d;
-            accepted[i - c0] = acc;
+    int gb[64], ge[64];
+    int ng = class_groups(g, cls, mode, gb, ge);
+    for (int k = 0; k < ng; ++k) {
+        int g0 = gb[k], g1 = ge[k];
+        for (int b0 = g0; b0 < g1; b0 += t->block) {
+            int b1 = b0 + t->block < g1 ? b0 + t->block : g1;
+            double d = 0.0;
+            for (int i = b0; i < b1; ++i) d += t->dEl[g->class_links[i]];
+            int acc = dist_to_window(E + d, lo, hi) <= dist_to_window(E, lo, hi);
+            for (int i = b0; i < b1; ++i) {
+                th_prop[i - c0] = t->prop[g->class_links[i]];
+                E_before[i - c0] = E;
+                dE_block[i - c0] = d;
+                accepted[i - c0] = acc;
+            }
+            if (acc) E += d;
         }
-        if (acc) E += d;
     }
     return c1 - c0;
 }
 
-/* One pass over all classes in the order mu = 0..d-1, parity 0,1. */
+/* One pass.  Heat-bath: the classes in the order mu = 0..d-1, parity 0,1,
+ * each over the whole lattice.  Overrelaxation: slab by slab (last
+ * coordinate), and within a slab the classes in the same order. */
 static void pass(orc_lat *t, int mode, double a, uint32_t tag)
 {
-    for (int cls = 0; cls < 2 * t->g->d; ++cls) class_pass(t, cls, mode, a, tag);
+    const orc_geom *g = t->g;
+    if (mode == 0) {
+        for (int cls = 0; cls < 2 * g->d; ++cls) class_pass(t, cls, mode, a, tag);
+        return;
+    }
+    for (int sl = 0; sl < g->dims[g->d - 1]; ++sl)
+        for (int cls = 0; cls < 2 * g->d; ++cls) {
+            int b, e;
+            slab_range(g, cls, sl, &b, &e);
+            group_update(t, b, e, mode, a, tag);
+        }
 }
 
 /* One composite sweep: heat-bath pass + n_or overrelaxation passes, then

@@ -14,6 +14,11 @@
 // Design
 //   * Links are float32 angles, SoA by (direction, site parity), sites of a
 //     parity in lexicographic order: theta[off + (2 mu + p) * V/2 + s/2].
+//   * A heat-bath pass runs class by class over the whole lattice (one
+//     pipeline drain per class); an overrelaxation pass is slab-major: for
+//     each x3 slab, all 8 checkerboard classes of that slab in order, so a
+//     slab's neighbourhood is reused from L2 by the 8 classes instead of each
+//     class streaming the whole lattice.
 //   * One persistent kernel.  Work items are (composite sweep j, lattice);
 //     a CTA takes the next item from an atomic counter, waits (bounded) until
 //     sweep j-1 of that lattice is done, and owns the lattice for that sweep.
@@ -222,8 +227,8 @@ struct Smem {
 // Producer side of one heat-bath class (MU, p): proposals and warp prefix
 // sums, chunk by chunk, into the stage ring (slope a_f, Philox tag `tag`).
 template <int MU, int NWP, bool FAST>
-__device__ __noinline__ void produce_class(Smem<NWP> &sm, const float *th, int p, float a_f, uint32_t tag,
-                              int B, int nchunk)
+__device__ __noinline__ void produce_class(Smem<NWP> &sm, const float *th, int p, float a_f,
+                                           uint32_t tag, int B, int h0, int count, int nchunk)
 {
     constexpr int NT = (NWP + 1) * 32, CH = NWP * 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -234,8 +239,9 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, const float *th, int p
     for (int ch = 0; ch < nchunk; ++ch) {
         const int s = ch & (kStages - 1);
         if (ch >= kStages) bar_sync(5 + s, NT);
-        const int h = ch * CH + tid;
-        const bool valid = h < half;
+        const int local = ch * CH + tid;
+        const int h = h0 + local;
+        const bool valid = local < count;
         float thn = 0.0f;
         long long d = 0;
         if (valid) {
@@ -268,7 +274,7 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, const float *th, int p
         const int bstart = lane & ~(B - 1);
         const long long Pprev = __shfl_sync(kFull, P, bstart > 0 ? bstart - 1 : 0);
         const long long bsum = P - (bstart > 0 ? Pprev : 0ll);
-        const bool isend = valid && (((lane & (B - 1)) == B - 1) || h == half - 1);
+        const bool isend = valid && (((lane & (B - 1)) == B - 1) || local == count - 1);
         const unsigned em = __ballot_sync(kFull, isend);
         Stage<NWP> &stg = sm.stage[s];
         stg.thn[tid] = thn;
@@ -285,13 +291,13 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, const float *th, int p
 // (the float32 rounding of E, ~1e-6 per link, is absorbed by the resync at
 // the end of the composite sweep).
 template <int MU, int NWP, bool FAST>
-__device__ __noinline__ void overrelax_class(Smem<NWP> &sm, float *th, int p)
+__device__ __noinline__ void overrelax_class(Smem<NWP> &sm, float *th, int p, int h0, int count)
 {
     constexpr int NT = (NWP + 1) * 32;
     const int L = sm.st.L, half = sm.st.half;
     const uint32_t magic = sm.st.magic;
     float *own = th + (2 * MU + p) * half;
-    for (int h = threadIdx.x; h < half; h += NT) {
+    for (int h = h0 + threadIdx.x; h < h0 + count; h += NT) {
         int x[4];
         const int site = decode_half(h, p, L, magic, x);
         float Sr, Si;
@@ -303,7 +309,8 @@ __device__ __noinline__ void overrelax_class(Smem<NWP> &sm, float *th, int p)
 // Consumer side: sequential Metropolis accept of the chunk's blocks in link
 // order, then the write of the accepted angles.  Runs in the last warp.
 template <int NWP>
-__device__ __noinline__ void consume_class(Smem<NWP> &sm, float *own, int half, int nchunk)
+__device__ __noinline__ void consume_class(Smem<NWP> &sm, float *own, int h0, int count,
+                                           int nchunk)
 {
     constexpr int NT = (NWP + 1) * 32, CH = NWP * 32;
     const int lane = threadIdx.x & 31;
@@ -341,11 +348,11 @@ __device__ __noinline__ void consume_class(Smem<NWP> &sm, float *own, int half, 
                     rem &= ~((2u << j) - 1u);
                 }
             }
-            const int h = ch * CH + g * 32 + lane;
-            if (h < half) {
+            const int local = ch * CH + g * 32 + lane;
+            if (local < count) {
                 const int eb = __ffs(em & ~((1u << lane) - 1u)) - 1;
                 if ((acc >> eb) & 1u) {
-                    own[h] = stg.thn[g * 32 + lane];
+                    own[h0 + local] = stg.thn[g * 32 + lane];
                     ++cnt;
                 }
             }
@@ -360,6 +367,10 @@ __device__ __noinline__ void consume_class(Smem<NWP> &sm, float *own, int half, 
     }
 }
 
+// One pass over the selected classes (mu = 0..3, parity 0,1).  Heat-bath:
+// class by class over the whole lattice.  Overrelaxation: slab by slab of the
+// last coordinate (x3 = t, the h range [t S, (t+1) S) of every class array,
+// S = L^3 / 2) and the classes within each slab.
 template <int NWP, bool FAST>
 __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t tag, int B,
                          int class_mask)
@@ -367,31 +378,47 @@ __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t
     constexpr int CH = NWP * 32;
     if (threadIdx.x == 0) sm.acc_cnt = 0ull;
     __syncthreads();
-    const int half = sm.st.half;
-    const int nchunk = (half + CH - 1) / CH;
-    const bool consumer = (threadIdx.x >> 5) == NWP;
+    const int half = sm.st.half, L = sm.st.L;
+    if (kind == 1) {
+        // Overrelaxation: slab by slab (x3), all classes within a slab, so the
+        // neighbours a slab's staples read are still in L2 from the class before.
+        const int S = half / L;
 #pragma unroll 1
-    for (int cls = 0; cls < 8; ++cls) {
-        if (!((class_mask >> cls) & 1)) continue;
-        const int mu = cls >> 1, p = cls & 1;
-        if (kind == 1) {
-            switch (mu) {
-                case 0: overrelax_class<0, NWP, FAST>(sm, th, p); break;
-                case 1: overrelax_class<1, NWP, FAST>(sm, th, p); break;
-                case 2: overrelax_class<2, NWP, FAST>(sm, th, p); break;
-                default: overrelax_class<3, NWP, FAST>(sm, th, p); break;
-            }
-        } else if (consumer) {
-            consume_class<NWP>(sm, th + (2 * mu + p) * half, half, nchunk);
-        } else {
-            switch (mu) {
-                case 0: produce_class<0, NWP, FAST>(sm, th, p, a_f, tag, B, nchunk); break;
-                case 1: produce_class<1, NWP, FAST>(sm, th, p, a_f, tag, B, nchunk); break;
-                case 2: produce_class<2, NWP, FAST>(sm, th, p, a_f, tag, B, nchunk); break;
-                default: produce_class<3, NWP, FAST>(sm, th, p, a_f, tag, B, nchunk); break;
+        for (int t = 0; t < L; ++t) {
+#pragma unroll 1
+            for (int cls = 0; cls < 8; ++cls) {
+                if (!((class_mask >> cls) & 1)) continue;
+                const int p = cls & 1;
+                switch (cls >> 1) {
+                    case 0: overrelax_class<0, NWP, FAST>(sm, th, p, t * S, S); break;
+                    case 1: overrelax_class<1, NWP, FAST>(sm, th, p, t * S, S); break;
+                    case 2: overrelax_class<2, NWP, FAST>(sm, th, p, t * S, S); break;
+                    default: overrelax_class<3, NWP, FAST>(sm, th, p, t * S, S); break;
+                }
+                __syncthreads();   // the next group reads the angles written here
             }
         }
-        __syncthreads();   // the next class reads the angles written here
+    } else {
+        // Heat-bath: one class at a time over the whole lattice, so the
+        // producer/consumer pipeline drains once per class.
+        const int nchunk = (half + CH - 1) / CH;
+        const bool consumer = (threadIdx.x >> 5) == NWP;
+#pragma unroll 1
+        for (int cls = 0; cls < 8; ++cls) {
+            if (!((class_mask >> cls) & 1)) continue;
+            const int mu = cls >> 1, p = cls & 1;
+            if (consumer) {
+                consume_class<NWP>(sm, th + (2 * mu + p) * half, 0, half, nchunk);
+            } else {
+                switch (mu) {
+                    case 0: produce_class<0, NWP, FAST>(sm, th, p, a_f, tag, B, 0, half, nchunk); break;
+                    case 1: produce_class<1, NWP, FAST>(sm, th, p, a_f, tag, B, 0, half, nchunk); break;
+                    case 2: produce_class<2, NWP, FAST>(sm, th, p, a_f, tag, B, 0, half, nchunk); break;
+                    default: produce_class<3, NWP, FAST>(sm, th, p, a_f, tag, B, 0, half, nchunk); break;
+                }
+            }
+            __syncthreads();   // the next class reads the angles written here
+        }
     }
     if (threadIdx.x == 0) {
         const unsigned long long n =

@@ -63,3 +63,37 @@ def batch_means(x, nbatch: int = 50):
     n = (len(x) // nbatch) * nbatch
     b = x[:n].reshape(nbatch, -1).mean(axis=1)
     return float(x[:n].mean()), float(b.std(ddof=1) / np.sqrt(nbatch))
+
+
+def restricted_moments_3plaq(lo: float, hi: float, a: float, kmax: int = 1, n_outer=600,
+                             n_inner=48):
+    """The same integrals for E = cos p1 + cos p2 + cos p3 (three independent
+    uniform plaquettes): Gauss-Legendre over (p1, p2) in [0, pi]^2 and, for each,
+    Gauss-Legendre over the p3 interval on which E lies in the window."""
+    xo, wo = np.polynomial.legendre.leggauss(n_outer)
+    xi, wi = np.polynomial.legendre.leggauss(n_inner)
+    u = 0.5 * np.pi * (xo + 1.0)
+    wu = 0.5 * np.pi * wo
+    cu = np.cos(u)
+    c = cu[:, None] + cu[None, :]
+    w2 = wu[:, None] * wu[None, :]
+    top = np.clip(hi - c, -1.0, 1.0)
+    bot = np.clip(lo - c, -1.0, 1.0)
+    ok = (hi - c >= -1.0) & (lo - c <= 1.0)
+    v1 = np.arccos(top)
+    v2 = np.arccos(bot)
+    half = 0.5 * (v2 - v1)
+    mid = 0.5 * (v2 + v1)
+    v = mid[..., None] + half[..., None] * xi[None, None, :]
+    E = c[..., None] + np.cos(v)
+    out = np.zeros(kmax + 1)
+    for k in range(kmax + 1):
+        f = E ** k * np.exp(-a * E)
+        inner = (f * wi[None, None, :]).sum(axis=-1) * half
+        out[k] = (w2 * np.where(ok, inner, 0.0)).sum() / np.pi ** 3
+    return out
+
+
+def restricted_mean_3plaq(lo, hi, a):
+    m = restricted_moments_3plaq(lo, hi, a, 1)
+    return m[1] / m[0]

@@ -178,6 +178,37 @@ def test_unrestricted_heat_bath_2d_open_gives_I1_over_I0():
     assert abs(m - exact2d.bessel_ratio(beta)) < 4 * err + 1e-12
 
 
+def test_three_plaquette_quadrature_is_self_consistent():
+    """The 3-plaquette quadrature reduces to known limits: the unrestricted mean
+    at weight exp(-aE) is 3 I1(-a)/I0(-a), and a window covering everything
+    gives the same."""
+    from scipy import special
+    a = -0.8
+    m = exact2d.restricted_moments_3plaq(-3.5, 3.5, a, 1)
+    assert abs(m[1] / m[0] - 3 * special.i1(-a) / special.i0(-a)) < 1e-6
+    assert abs(m[0] - special.i0(-a) ** 3) < 1e-6
+
+
+def test_three_plaquette_blocks_of_two_are_exact():
+    """4x2 open strip (3 plaquettes): a slab of one class holds two links, so
+    with B = 2 the window decides two-link blocks; the chain still reproduces
+    the restricted mean of eq. kk9."""
+    lo, hi, a = 0.9, 1.6, -1.0
+    g = oracle.Geom([4, 2], periodic=False)
+    assert g.nplaq == 3
+    t = oracle.Lattice(g, 4321, 2, 0, lo, hi - lo, n_or=1, block=2)
+    t.hot_start()
+    assert t.approach(10000) >= 0
+    es = []
+    for _ in range(40000):
+        t.sweep(a, 1)
+        es.append(t.E)
+    es = np.array(es)
+    assert np.all(es >= lo - 1e-12) and np.all(es <= hi + 1e-12)
+    m, err = exact2d.batch_means(es)
+    assert abs(m - exact2d.restricted_mean_3plaq(lo, hi, a)) < 4 * err
+
+
 @pytest.mark.parametrize("block,a", [(1, -1.0), (2, 2.0), (1, 4.0)])
 def test_two_plaquette_restricted_mean_is_exact(block, a):
     """2x1 plaquette strip (7 links): the restricted chain reproduces eq. kk9."""
