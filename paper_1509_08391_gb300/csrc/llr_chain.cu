@@ -62,18 +62,19 @@ constexpr int kStages = 4;
 // z = cos(pi u1), f = (1 + r z) / (r + z), c = k (r - f); accept if
 // c (2 - c) > u2 or ln(c / u2) + 1 - c >= 0.  The accept test runs on fast
 // hardware approximations (it only decides which attempt is taken); the
-// accepted variate is then evaluated accurately: acos(f) as
-// 2 asin(sqrt((1-f)/2)) or pi - 2 asin(sqrt((1+f)/2)) with 1 -+ f formed
-// without cancellation, so small and near-pi angles keep full precision.
+// accepted variate is then evaluated accurately as (cos X, sin X), X = +-acos f:
+// with sh, ch = sin, cos(pi u1 / 2), z = ch^2 - sh^2 and
+//   1 - f = (r - 1) 2 sh^2 / (r + z)   (f >= 0),   1 + f = (r + 1) 2 ch^2 / (r + z)   (f < 0),
+// so w = 1 -+ f has no cancellation, cos X = +-(1 - w) and
+// |sin X| = sqrt(w (2 - w)) keep full precision near X = 0 and X = pi.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool von_mises(float kappa, uint32_t c0, uint32_t c1, uint32_t c2,
-                                          uint32_t k0, uint32_t k1, float &X, float &cX)
+                                          uint32_t k0, uint32_t k1, float &cX, float &sX)
 {
     if (fabsf(kappa) < 1e-6f) {
         const U4 w = philox4x32_10(c0, c1, c2, 0u, k0, k1);
-        const float t = 2.0f * u01(w.x) - 1.0f;
-        X = kPi * t;
-        cX = cospif(t);
+        const float t = 2.0f * u01(w.x) - 1.0f;   // X = pi t
+        sincospif(t, &sX, &cX);
         return true;
     }
     const float k = fabsf(kappa);
@@ -106,25 +107,18 @@ __device__ __forceinline__ bool von_mises(float kappa, uint32_t c0, uint32_t c1,
     if (!found) return false;
     // ... then evaluate the accepted variate once, accurately
     const float u1 = u01(w_acc);
-    const float z = cospif(u1);
+    float sh, ch;
+    sincospif(0.5f * u1, &sh, &ch);
+    const float z = (ch - sh) * (ch + sh);
     const float den = r + z;
-    const float f = (1.0f + r * z) / den;
-    float mag, fa;
-    if (f >= 0.0f) {
-        const float sh = sinpif(0.5f * u1);
-        const float g = rm1 * 2.0f * sh * sh / den;            // 1 - f
-        mag = 2.0f * asinf(fminf(sqrtf(0.5f * g), 1.0f));
-        fa = 1.0f - g;
-    } else {
-        const float ch = cospif(0.5f * u1);
-        const float hp = (r + 1.0f) * 2.0f * ch * ch / den;    // 1 + f
-        mag = kPi - 2.0f * asinf(fminf(sqrtf(0.5f * hp), 1.0f));
-        fa = hp - 1.0f;
-    }
-    float x = (w_acc & 1u) ? mag : -mag;
-    if (kappa < 0.0f) x = wrap_angle(x + kPi);
-    X = x;
-    cX = kappa < 0.0f ? -fa : fa;
+    const bool pos = 1.0f + r * z >= 0.0f;                   // f >= 0
+    const float w = (pos ? rm1 * 2.0f * sh * sh : (r + 1.0f) * 2.0f * ch * ch) / den;
+    const float s = sqrtf(fmaxf(w * (2.0f - w), 0.0f));
+    const float c = pos ? 1.0f - w : w - 1.0f;
+    const bool neg_x = !(w_acc & 1u);                        // X = -acos f
+    const bool flip = kappa < 0.0f;                          // X -> X + pi
+    cX = flip ? -c : c;
+    sX = (neg_x != flip) ? -s : s;
     return true;
 }
 
@@ -157,19 +151,44 @@ __device__ __forceinline__ int decode_half(int h, int p, int L, uint32_t magic, 
 // forward  phi = theta_nu(x+mu) - theta_mu(x+nu) - theta_nu(x)
 // backward phi = theta_nu(x-nu) - theta_nu(x-nu+mu) - theta_mu(x-nu)
 // so that the link's local energy is sum_j cos(theta + phi_j) = Re(e^{i theta} S).
-// Plain (coherent) loads: other classes of this lattice were written earlier
-// in the same launch.
-template <int MU, bool FAST>
-__device__ __forceinline__ void staple_sum(const float *th, int half, int L, const int x[4], int s,
-                                           int p, float &Sr, float &Si)
+//
+// The 18 neighbour angles are staged through shared memory: staple_fetch
+// issues one 4-byte asynchronous copy (cp.async, cached in L1) per angle into
+// the calling thread's column of a stage buffer, staple_from sums the staples
+// from it once the copies have landed.  A thread only reads what it copied
+// itself, so cp.async.wait_group is the only synchronisation.  The copies
+// read through L1 like plain loads: other classes of this lattice were
+// written earlier in the same launch (same CTA, or another CTA before the
+// acquire of the lattice's done counter).
+constexpr int kStaged = 18;   // angles per link in a stage column
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Stage the neighbour angles of link theta_MU(x) (site s, parity p) into
+// col[k * stride], k = 6 j + (a1, a2, a3, b1, b2, b3) for the j-th nu != MU.
+template <int MU>
+__device__ __forceinline__ void staple_fetch(const float *th, int half, int L, const int x[4],
+                                             int s, int p, float *col, int stride)
 {
     const int st[4] = {1, L, L * L, L * L * L};
     const int dmu = (x[MU] == L - 1) ? -(L - 1) * st[MU] : st[MU];
     const int spmu = s + dmu;
     const int q = p ^ 1;
     const float *thmu_q = th + (2 * MU + q) * half;
-    Sr = 0.0f;
-    Si = 0.0f;
+    int j = 0;
 #pragma unroll
     for (int nu = 0; nu < 4; ++nu) {
         if (nu == MU) continue;
@@ -180,20 +199,44 @@ __device__ __forceinline__ void staple_sum(const float *th, int half, int L, con
         const int smnu_pmu = smnu + dmu;
         const float *thnu_p = th + (2 * nu + p) * half;
         const float *thnu_q = th + (2 * nu + q) * half;
-        const float a1 = thnu_q[spmu >> 1];      // theta_nu(x+mu)
-        const float a2 = thmu_q[spnu >> 1];      // theta_mu(x+nu)
-        const float a3 = thnu_p[s >> 1];         // theta_nu(x)
-        const float b1 = thnu_p[smnu_pmu >> 1];  // theta_nu(x-nu+mu)
-        const float b2 = thmu_q[smnu >> 1];      // theta_mu(x-nu)
-        const float b3 = thnu_q[smnu >> 1];      // theta_nu(x-nu)
-        const float pf = a1 - a2 - a3;
-        const float pb = b3 - b1 - b2;
+        float *c = col + 6 * j * stride;
+        cp_async4(c + 0 * stride, thnu_q + (spmu >> 1));      // theta_nu(x+mu)
+        cp_async4(c + 1 * stride, thmu_q + (spnu >> 1));      // theta_mu(x+nu)
+        cp_async4(c + 2 * stride, thnu_p + (s >> 1));         // theta_nu(x)
+        cp_async4(c + 3 * stride, thnu_p + (smnu_pmu >> 1));  // theta_nu(x-nu+mu)
+        cp_async4(c + 4 * stride, thmu_q + (smnu >> 1));      // theta_mu(x-nu)
+        cp_async4(c + 5 * stride, thnu_q + (smnu >> 1));      // theta_nu(x-nu)
+        ++j;
+    }
+}
+
+template <bool FAST>
+__device__ __forceinline__ void staple_from(const float *col, int stride, float &Sr, float &Si)
+{
+    Sr = 0.0f;
+    Si = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float *c = col + 6 * j * stride;
+        const float pf = c[0] - c[stride] - c[2 * stride];
+        const float pb = c[5 * stride] - c[3 * stride] - c[4 * stride];
         float sf, cf, sb, cb;
         sin_cos<FAST>(pf, &sf, &cf);
         sin_cos<FAST>(pb, &sb, &cb);
         Sr += cf + cb;
         Si += sf + sb;
     }
+}
+
+// The stage buffer (dynamic shared memory): two columns sets of kStaged x NT
+// floats, so the copies for a thread's next link land while it works on the
+// current one.
+extern __shared__ __align__(16) float g_stage_buf[];
+
+template <int NT>
+__device__ __forceinline__ float *stage_col(int buf)
+{
+    return g_stage_buf + buf * kStaged * NT + threadIdx.x;
 }
 
 // Named barriers 1..8 (0 is __syncthreads): stage s is full (1 + s) / empty (5 + s).
@@ -236,29 +279,51 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, const float *th, int p
     const uint32_t magic = sm.st.magic, V = 2u * (uint32_t)half;
     const uint32_t k0 = sm.st.key0, k1 = sm.st.key1, sweep = sm.st.sweep;
     const float *own = th + (2 * MU + p) * half;
+    // prologue: stage the first chunk's neighbours
+    bool valid_n = tid < count;
+    int site_n = 0;
+    float t0_n = 0.0f;
+    if (valid_n) {
+        int x[4];
+        site_n = decode_half(h0 + tid, p, L, magic, x);
+        staple_fetch<MU>(th, half, L, x, site_n, p, stage_col<NT>(0), NT);
+        t0_n = own[h0 + tid];
+    }
+    cp_async_commit();
     for (int ch = 0; ch < nchunk; ++ch) {
         const int s = ch & (kStages - 1);
-        if (ch >= kStages) bar_sync(5 + s, NT);
         const int local = ch * CH + tid;
-        const int h = h0 + local;
-        const bool valid = local < count;
+        const bool valid = valid_n;
+        const int site = site_n;
+        const float t0 = t0_n;
+        // stage the next chunk's neighbours while this one is sampled
+        {
+            const int ln = local + CH;
+            valid_n = ch + 1 < nchunk && ln < count;
+            if (valid_n) {
+                int x[4];
+                site_n = decode_half(h0 + ln, p, L, magic, x);
+                staple_fetch<MU>(th, half, L, x, site_n, p, stage_col<NT>((ch + 1) & 1), NT);
+                t0_n = own[h0 + ln];
+            }
+            cp_async_commit();
+        }
+        if (ch >= kStages) bar_sync(5 + s, NT);
+        cp_async_wait<1>();
         float thn = 0.0f;
         long long d = 0;
         if (valid) {
-            int x[4];
-            const int site = decode_half(h, p, L, magic, x);
             float Sr, Si;
-            staple_sum<MU, FAST>(th, half, L, x, site, p, Sr, Si);
-            const float t0 = own[h];
+            staple_from<FAST>(stage_col<NT>(ch & 1), NT, Sr, Si);
             float so, co;
             sincosf(t0, &so, &co);   // accurate: a biased cosine here biases every dE
             const float e_old = co * Sr - so * Si;     // |S| cos(theta + alpha)
-            const float alpha = atan2f(Si, Sr);
             const float Sabs = sqrtf(Sr * Sr + Si * Si);
-            float X, cX;
+            float cX, sX;
             const uint32_t link = (uint32_t)MU * V + (uint32_t)site;
-            if (von_mises(-a_f * Sabs, link, sweep, tag, k0, k1, X, cX)) {
-                thn = wrap_angle(X - alpha);
+            if (von_mises(-a_f * Sabs, link, sweep, tag, k0, k1, cX, sX)) {
+                // theta' = X - alpha, alpha = arg S: e^{i theta'} = e^{iX} conj(S) / |S|
+                thn = atan2f(sX * Sr - cX * Si, cX * Sr + sX * Si);
                 d = to_fx(Sabs * cX - e_old);            // theta' + alpha = X
             } else {
                 thn = t0;
@@ -283,6 +348,7 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, const float *th, int p
         if (lane == 0) stg.endmask[warp] = em;
         bar_arrive(1 + s, NT);
     }
+    cp_async_wait<0>();
 }
 
 // One overrelaxation class (MU, p): theta' = -theta - 2 alpha keeps
@@ -297,13 +363,35 @@ __device__ __noinline__ void overrelax_class(Smem<NWP> &sm, float *th, int p, in
     const int L = sm.st.L, half = sm.st.half;
     const uint32_t magic = sm.st.magic;
     float *own = th + (2 * MU + p) * half;
-    for (int h = h0 + threadIdx.x; h < h0 + count; h += NT) {
+    const int tid = threadIdx.x;
+    bool valid_n = tid < count;
+    float t0_n = 0.0f;
+    if (valid_n) {
         int x[4];
-        const int site = decode_half(h, p, L, magic, x);
-        float Sr, Si;
-        staple_sum<MU, FAST>(th, half, L, x, site, p, Sr, Si);
-        own[h] = wrap_angle(-own[h] - 2.0f * atan2f(Si, Sr));
+        const int site = decode_half(h0 + tid, p, L, magic, x);
+        staple_fetch<MU>(th, half, L, x, site, p, stage_col<NT>(0), NT);
+        t0_n = own[h0 + tid];
     }
+    cp_async_commit();
+    for (int it = 0, local = tid; local < count; ++it, local += NT) {
+        const float t0 = t0_n;
+        {
+            const int ln = local + NT;
+            valid_n = ln < count;
+            if (valid_n) {
+                int x[4];
+                const int site = decode_half(h0 + ln, p, L, magic, x);
+                staple_fetch<MU>(th, half, L, x, site, p, stage_col<NT>((it + 1) & 1), NT);
+                t0_n = own[h0 + ln];
+            }
+            cp_async_commit();
+        }
+        cp_async_wait<1>();
+        float Sr, Si;
+        staple_from<FAST>(stage_col<NT>(it & 1), NT, Sr, Si);
+        own[h0 + local] = wrap_angle(-t0 - 2.0f * atan2f(Si, Sr));
+    }
+    cp_async_wait<0>();
 }
 
 // Consumer side: sequential Metropolis accept of the chunk's blocks in link
@@ -791,7 +879,12 @@ __global__ void from_canonical_kernel(const LatState *lat, float *theta, const f
     }
 }
 
-// Resident CTAs of one kernel variant (queried once per process and device).
+// Dynamic shared memory of one kernel variant: the two stage column sets.
+template <int NWP>
+constexpr size_t stage_bytes() { return 2u * kStaged * (NWP + 1) * 32 * sizeof(float); }
+
+// Resident CTAs of one kernel variant (queried once per process and device;
+// also raises the variant's dynamic shared memory limit on that device).
 template <int NWP, bool FAST>
 int resident_ctas()
 {
@@ -801,8 +894,10 @@ int resident_ctas()
     if (dev < 0 || dev >= 64) dev = 0;
     if (cached[dev] == 0) {
         int per_sm = 0, sms = 0;
+        cudaFuncSetAttribute(llr_kernel<NWP, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)stage_bytes<NWP>());
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, llr_kernel<NWP, FAST>,
-                                                      (NWP + 1) * 32, 0);
+                                                      (NWP + 1) * 32, stage_bytes<NWP>());
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cached[dev] = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
     }
@@ -819,7 +914,7 @@ cudaError_t launch_t(const KernelArgs &a, cudaStream_t s)
     const int grid = (int)(items < cap ? items : cap);
     cudaError_t e = cudaMemsetAsync(a.sync, 0, sizeof(unsigned) * (size_t)(2 + a.n_lat), s);
     if (e != cudaSuccess) return e;
-    llr_kernel<NWP, FAST><<<grid, (NWP + 1) * 32, 0, s>>>(a);
+    llr_kernel<NWP, FAST><<<grid, (NWP + 1) * 32, stage_bytes<NWP>(), s>>>(a);
     return cudaGetLastError();
 }
 
