@@ -205,8 +205,9 @@ int llr_observables_noalloc(int n, const double *centres, const double *a, int n
 int llr_cv_peak(int n, const double *centres, const double *a, double beta_lo, double beta_hi,
                 int n_grid, double tol, double *out);
 
-/* Launch shape of the batched sweep kernel: threads per CTA (128, 256 or
- * 512; one CTA owns one lattice) and fast_math (1: hardware sine/cosine
+/* Launch shape of the batched sweep kernel: threads per CTA (128, 160, 192,
+ * 256 or 512; one warp scans the window decisions, the others propose; one
+ * CTA owns one lattice) and fast_math (1: hardware sine/cosine
  * approximations for the staples, 0: correctly rounded-class sincosf).
  * Chosen per lattice size by the autotuner; default 256 threads, fast math. */
 int llr_set_kernel_config(llr_handle h, int threads, int fast_math);

@@ -1,6 +1,6 @@
 """Autotuner of the batched sweep kernel's launch shape.
 
-The three CTA shapes (128, 256, 512 threads; one consumer warp, the rest
+The CTA shapes (128, 160, 192, 256, 512 threads; one consumer warp, the rest
 producers) run identical per-link arithmetic, so the choice changes speed
 only, never results.  For a workload the tuner builds a scratch batch of the
 same lattices (the caller's chains are not advanced), times one composite
@@ -17,7 +17,7 @@ import numpy as np
 from . import llr, workloads
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
-SHAPES = (128, 256, 512)
+SHAPES = (128, 160, 192, 256, 512)
 
 
 def _key(w: workloads.Workload, gpu: str) -> str:

@@ -525,8 +525,8 @@ int llr_status(llr_handle h, int *out)
 int llr_set_kernel_config(llr_handle h, int threads, int fast_math)
 {
     if (int r = check_handle(h)) return r;
-    if (threads != 128 && threads != 256 && threads != 512)
-        return fail(LLR_ERR_ARG, "threads must be 128, 256 or 512");
+    if (threads != 128 && threads != 160 && threads != 192 && threads != 256 && threads != 512)
+        return fail(LLR_ERR_ARG, "threads must be 128, 160, 192, 256 or 512");
     h->cfg.threads = threads;
     h->cfg.fast_math = fast_math != 0;
     return LLR_OK;

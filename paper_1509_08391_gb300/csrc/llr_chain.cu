@@ -252,9 +252,9 @@ __device__ __forceinline__ void bar_arrive(int id, int n)
 template <int NWP>
 struct Stage {
     float thn[NWP * 32];
-    long long P[NWP * 32];
-    long long bs[NWP * 32];
+    long long P[NWP * 32];   // warp-inclusive prefix sums of dE (fixed point)
     unsigned endmask[NWP];
+    unsigned accmask[NWP];   // written by the consumer: accepted block ends
 };
 
 template <int NWP>
@@ -265,34 +265,53 @@ struct Smem {
     unsigned long long acc_cnt;
     unsigned long long cap_cnt;
     int item_lat, item_j, item_state;
+    int cw;   // the consumer warp of a heat-bath pass
 };
 
 // Producer side of one heat-bath class (MU, p): proposals and warp prefix
 // sums, chunk by chunk, into the stage ring (slope a_f, Philox tag `tag`).
+// When a slot comes back from the consumer (and for the last chunks at the
+// end of the class) each producer writes its link's proposal if the
+// consumer accepted the block it belongs to.
 template <int MU, int NWP, bool FAST>
-__device__ __noinline__ void produce_class(Smem<NWP> &sm, const float *th, int p, float a_f,
+__device__ __noinline__ void produce_class(Smem<NWP> &sm, float *th, int p, float a_f,
                                            uint32_t tag, int B, int h0, int count, int nchunk)
 {
     constexpr int NT = (NWP + 1) * 32, CH = NWP * 32;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // producer rank pt (0 .. CH-1) and producer warp pw: the warps other
+    // than the consumer warp sm.cw, in order
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int pw = w - (w > sm.cw ? 1 : 0), pt = pw * 32 + lane;
     const int L = sm.st.L, half = sm.st.half;
     const uint32_t magic = sm.st.magic, V = 2u * (uint32_t)half;
     const uint32_t k0 = sm.st.key0, k1 = sm.st.key1, sweep = sm.st.sweep;
-    const float *own = th + (2 * MU + p) * half;
+    float *own = th + (2 * MU + p) * half;
+    unsigned cnt = 0;
+    // write back chunk c of a slot the consumer has released
+    auto flush = [&](const Stage<NWP> &stg, int c) {
+        const int lc = c * CH + pt;
+        if (lc < count) {
+            const int eb = __ffs(stg.endmask[pw] & ~((1u << lane) - 1u)) - 1;
+            if ((stg.accmask[pw] >> eb) & 1u) {
+                own[h0 + lc] = stg.thn[pt];
+                ++cnt;
+            }
+        }
+    };
     // prologue: stage the first chunk's neighbours
-    bool valid_n = tid < count;
+    bool valid_n = pt < count;
     int site_n = 0;
     float t0_n = 0.0f;
     if (valid_n) {
         int x[4];
-        site_n = decode_half(h0 + tid, p, L, magic, x);
+        site_n = decode_half(h0 + pt, p, L, magic, x);
         staple_fetch<MU>(th, half, L, x, site_n, p, stage_col<NT>(0), NT);
-        t0_n = own[h0 + tid];
+        t0_n = own[h0 + pt];
     }
     cp_async_commit();
     for (int ch = 0; ch < nchunk; ++ch) {
         const int s = ch & (kStages - 1);
-        const int local = ch * CH + tid;
+        const int local = ch * CH + pt;
         const bool valid = valid_n;
         const int site = site_n;
         const float t0 = t0_n;
@@ -308,7 +327,10 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, const float *th, int p
             }
             cp_async_commit();
         }
-        if (ch >= kStages) bar_sync(5 + s, NT);
+        if (ch >= kStages) {
+            bar_sync(5 + s, NT);
+            flush(sm.stage[s], ch - kStages);
+        }
         cp_async_wait<1>();
         float thn = 0.0f;
         long long d = 0;
@@ -336,19 +358,23 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, const float *th, int p
             const long long y = __shfl_up_sync(kFull, P, o);
             if (lane >= o) P += y;
         }
-        const int bstart = lane & ~(B - 1);
-        const long long Pprev = __shfl_sync(kFull, P, bstart > 0 ? bstart - 1 : 0);
-        const long long bsum = P - (bstart > 0 ? Pprev : 0ll);
         const bool isend = valid && (((lane & (B - 1)) == B - 1) || local == count - 1);
         const unsigned em = __ballot_sync(kFull, isend);
         Stage<NWP> &stg = sm.stage[s];
-        stg.thn[tid] = thn;
-        stg.P[tid] = P;
-        stg.bs[tid] = bsum;
-        if (lane == 0) stg.endmask[warp] = em;
+        stg.thn[pt] = thn;
+        stg.P[pt] = P;
+        if (lane == 0) stg.endmask[pw] = em;
         bar_arrive(1 + s, NT);
     }
+    for (int c = nchunk > kStages ? nchunk - kStages : 0; c < nchunk; ++c) {
+        const int s = c & (kStages - 1);
+        bar_sync(5 + s, NT);
+        flush(sm.stage[s], c);
+    }
     cp_async_wait<0>();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
+    if (lane == 0) atomicAdd(&sm.acc_cnt, (unsigned long long)cnt);
 }
 
 // One overrelaxation class (MU, p): theta' = -theta - 2 alpha keeps
@@ -395,64 +421,83 @@ __device__ __noinline__ void overrelax_class(Smem<NWP> &sm, float *th, int p, in
 }
 
 // Consumer side: sequential Metropolis accept of the chunk's blocks in link
-// order, then the write of the accepted angles.  Runs in the last warp.
+// order; publishes the accepted block ends of each group (the producers
+// write the angles).  Runs in the last warp.
 template <int NWP>
-__device__ __noinline__ void consume_class(Smem<NWP> &sm, float *own, int h0, int count,
-                                           int nchunk)
+__device__ __noinline__ void consume_class(Smem<NWP> &sm, int B, int nchunk)
 {
-    constexpr int NT = (NWP + 1) * 32, CH = NWP * 32;
+    constexpr int NT = (NWP + 1) * 32;
     const int lane = threadIdx.x & 31;
     long long E = sm.st.E_fx;
     const long long lo = sm.st.lo_fx, hi = sm.st.hi_fx;
-    unsigned cnt = 0;
     for (int ch = 0; ch < nchunk; ++ch) {
         const int s = ch & (kStages - 1);
         bar_sync(1 + s, NT);
-        const Stage<NWP> &stg = sm.stage[s];
+        Stage<NWP> &stg = sm.stage[s];
         for (int g = 0; g < NWP; ++g) {
             const unsigned em = stg.endmask[g];
             unsigned rem = em, acc = 0u;
             const long long Pk = stg.P[g * 32 + lane];
-            const long long bk = stg.bs[g * 32 + lane];
-            long long base = 0;
-            while (rem) {
-                const long long Ea = E + (Pk - base);
-                const long long Eb = Ea - bk;
-                const bool mine = (rem >> lane) & 1u;
-                const bool viol = mine && (dist_fx(Ea, lo, hi) > dist_fx(Eb, lo, hi));
-                const unsigned vm = __ballot_sync(kFull, viol);
-                if (vm == 0u) {
-                    const int last = 31 - __clz(rem);
-                    E += __shfl_sync(kFull, Pk, last) - base;
-                    acc |= rem;
-                    rem = 0u;
-                } else {
+            // the sum of the block ending at this lane (blocks of B links
+            // start at multiples of B within the group)
+            const int bstart = lane & ~(B - 1);
+            const long long Pprev = __shfl_sync(kFull, Pk, bstart > 0 ? bstart - 1 : 0);
+            const long long bk = Pk - (bstart > 0 ? Pprev : 0ll);
+            if (em != 0u && E >= lo && E <= hi) {
+                // Inside the window (the usual case, and E stays inside): a
+                // block is accepted iff the energy after it is inside, i.e.
+                // lo - E <= Pk - R <= hi - E with R the sum of the blocks
+                // rejected so far.  Keep the bounds rlo = lo - E + R,
+                // rhi = hi - E + R; a rejection at j adds its block sum bj.
+                long long rlo = lo - E, rhi = hi - E;
+                while (rem) {
+                    const bool mine = (rem >> lane) & 1u;
+                    const bool viol = mine && (Pk < rlo || Pk > rhi);
+                    const unsigned vm = __ballot_sync(kFull, viol);
+                    if (vm == 0u) {
+                        acc |= rem;
+                        break;
+                    }
                     const int j = __ffs(vm) - 1;
                     acc |= rem & ((1u << j) - 1u);
-                    const long long Pj = __shfl_sync(kFull, Pk, j);
                     const long long bj = __shfl_sync(kFull, bk, j);
-                    E += (Pj - bj) - base;   // energy before the rejected block
-                    base = Pj;               // skip its contribution
+                    rlo += bj;
+                    rhi += bj;
                     rem &= ~((2u << j) - 1u);
                 }
-            }
-            const int local = ch * CH + g * 32 + lane;
-            if (local < count) {
-                const int eb = __ffs(em & ~((1u << lane) - 1u)) - 1;
-                if ((acc >> eb) & 1u) {
-                    own[h0 + local] = stg.thn[g * 32 + lane];
-                    ++cnt;
+                // E after the group = E + P_last - R = lo + P_last - rlo
+                E = lo + __shfl_sync(kFull, Pk, 31 - __clz(em)) - rlo;
+            } else {
+                // General rule (outside the window): accept iff
+                // dist(E + dE_block) <= dist(E).
+                long long base = 0;
+                while (rem) {
+                    const long long Ea = E + (Pk - base);
+                    const long long Eb = Ea - bk;
+                    const bool mine = (rem >> lane) & 1u;
+                    const bool viol = mine && (dist_fx(Ea, lo, hi) > dist_fx(Eb, lo, hi));
+                    const unsigned vm = __ballot_sync(kFull, viol);
+                    if (vm == 0u) {
+                        const int last = 31 - __clz(rem);
+                        E += __shfl_sync(kFull, Pk, last) - base;
+                        acc |= rem;
+                        rem = 0u;
+                    } else {
+                        const int j = __ffs(vm) - 1;
+                        acc |= rem & ((1u << j) - 1u);
+                        const long long Pj = __shfl_sync(kFull, Pk, j);
+                        const long long bj = __shfl_sync(kFull, bk, j);
+                        E += (Pj - bj) - base;   // energy before the rejected block
+                        base = Pj;               // skip its contribution
+                        rem &= ~((2u << j) - 1u);
+                    }
                 }
             }
+            if (lane == 0) stg.accmask[g] = acc;
         }
-        if (ch + kStages < nchunk) bar_arrive(5 + s, NT);
+        bar_arrive(5 + s, NT);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(kFull, cnt, o);
-    if (lane == 0) {
-        sm.st.E_fx = E;
-        sm.acc_cnt += cnt;
-    }
+    if (lane == 0) sm.st.E_fx = E;
 }
 
 // One pass over the selected classes (mu = 0..3, parity 0,1).  Heat-bath:
@@ -490,13 +535,13 @@ __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t
         // Heat-bath: one class at a time over the whole lattice, so the
         // producer/consumer pipeline drains once per class.
         const int nchunk = (half + CH - 1) / CH;
-        const bool consumer = (threadIdx.x >> 5) == NWP;
+        const bool consumer = (threadIdx.x >> 5) == sm.cw;
 #pragma unroll 1
         for (int cls = 0; cls < 8; ++cls) {
             if (!((class_mask >> cls) & 1)) continue;
             const int mu = cls >> 1, p = cls & 1;
             if (consumer) {
-                consume_class<NWP>(sm, th + (2 * mu + p) * half, 0, half, nchunk);
+                consume_class<NWP>(sm, B, nchunk);
             } else {
                 switch (mu) {
                     case 0: produce_class<0, NWP, FAST>(sm, th, p, a_f, tag, B, 0, half, nchunk); break;
@@ -657,9 +702,13 @@ __device__ __noinline__ void rm_update(LatState &st, const KernelArgs &args, int
 }
 
 // Resident CTAs per SM the register budget is held to: 128 threads x 8 and
-// 512 threads x 2 (64 registers), 256 threads x 3 (80 registers).
+// 512 threads x 2 (64 registers); 160 threads x 5, 192 threads x 4 and
+// 256 threads x 3 (80 registers).
 template <int NWP>
-constexpr int min_ctas() { return NWP == 3 ? 8 : (NWP == 7 ? 3 : 2); }
+constexpr int min_ctas()
+{
+    return NWP == 3 ? 8 : NWP == 4 ? 5 : NWP == 5 ? 4 : NWP == 7 ? 3 : 2;
+}
 
 template <int NWP, bool FAST>
 __global__ void __launch_bounds__((NWP + 1) * 32, min_ctas<NWP>()) llr_kernel(KernelArgs args)
@@ -672,6 +721,8 @@ __global__ void __launch_bounds__((NWP + 1) * 32, min_ctas<NWP>()) llr_kernel(Ke
     unsigned *counter = args.sync;
     unsigned *err = args.sync + 1;
     unsigned *done = args.sync + 2;
+    if (tid == 0) sm.cw = NWP;   // the consumer warp of a heat-bath pass: the last
+    __syncthreads();
     for (;;) {
         if (tid == 0) {
             const unsigned i = atomicAdd(counter, 1u);
@@ -922,23 +973,27 @@ cudaError_t launch_t(const KernelArgs &a, cudaStream_t s)
 
 void prime_launch(const LaunchCfg &cfg)
 {
-    if (cfg.threads == 128) {
-        if (cfg.fast_math) resident_ctas<3, true>(); else resident_ctas<3, false>();
-    } else if (cfg.threads == 512) {
-        if (cfg.fast_math) resident_ctas<15, true>(); else resident_ctas<15, false>();
-    } else {
-        if (cfg.fast_math) resident_ctas<7, true>(); else resident_ctas<7, false>();
+    const bool f = cfg.fast_math != 0;
+    switch (cfg.threads) {
+        case 128: f ? resident_ctas<3, true>() : resident_ctas<3, false>(); break;
+        case 160: f ? resident_ctas<4, true>() : resident_ctas<4, false>(); break;
+        case 192: f ? resident_ctas<5, true>() : resident_ctas<5, false>(); break;
+        case 512: f ? resident_ctas<15, true>() : resident_ctas<15, false>(); break;
+        default: f ? resident_ctas<7, true>() : resident_ctas<7, false>(); break;
     }
 }
 
 cudaError_t launch_llr(const KernelArgs &a, const LaunchCfg &cfg, cudaStream_t s)
 {
     if (a.n_lat <= 0) return cudaSuccess;
-    if (cfg.threads == 128)
-        return cfg.fast_math ? launch_t<3, true>(a, s) : launch_t<3, false>(a, s);
-    if (cfg.threads == 512)
-        return cfg.fast_math ? launch_t<15, true>(a, s) : launch_t<15, false>(a, s);
-    return cfg.fast_math ? launch_t<7, true>(a, s) : launch_t<7, false>(a, s);
+    const bool f = cfg.fast_math != 0;
+    switch (cfg.threads) {
+        case 128: return f ? launch_t<3, true>(a, s) : launch_t<3, false>(a, s);
+        case 160: return f ? launch_t<4, true>(a, s) : launch_t<4, false>(a, s);
+        case 192: return f ? launch_t<5, true>(a, s) : launch_t<5, false>(a, s);
+        case 512: return f ? launch_t<15, true>(a, s) : launch_t<15, false>(a, s);
+        default: return f ? launch_t<7, true>(a, s) : launch_t<7, false>(a, s);
+    }
 }
 
 __global__ void step_increment_kernel(int *step)

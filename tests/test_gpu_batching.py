@@ -82,10 +82,10 @@ def test_uneven_batch_equals_separate_batches():
 
 
 def test_kernel_shapes_give_identical_chains():
-    """128, 256 and 512 threads per CTA run the same per-link arithmetic."""
+    """Every CTA shape (128 ... 512 threads) runs the same per-link arithmetic."""
     w = workloads.subset(workloads.small_l4(), range(4))
     outs = []
-    for t in (128, 256, 512):
+    for t in (128, 160, 192, 256, 512):
         with llr.Batch.from_workload(w, max_approach=0) as b:
             b.set_kernel_config(t, True)
             b.approach(1000)
