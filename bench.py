@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--n-rm", type=int, default=150)
     p.add_argument("--phases", action="store_true",
                    help="profiling driver: one overrelaxation pass, one heat-bath pass and one "
-                        "composite sweep of 512 lattices of the workload (for ncu)")
+                        "composite sweep of 456 lattices of the workload (for ncu)")
     return p.parse_args()
 
 
@@ -141,8 +141,9 @@ def config_dict(args, w, world):
             "l2": "inputs larger than L2 (5.2 GB of links per GPU)"}
 
 
-def cpu_baseline(w, n_sweeps=1, max_lat=None):
-    """The FP64 oracle on a bounded sample of the same workload (host cores)."""
+def cpu_baseline(w, n_sweeps=8, max_lat=None):
+    """The FP64 oracle on a bounded sample of the same workload (host cores):
+    one lattice per core, n_sweeps composite sweeps (about 10 s on 16 cores)."""
     import oracle
     cores = os.cpu_count() or 1
     n = min(cores, w.n_lattices) if max_lat is None else max_lat
@@ -408,15 +409,16 @@ def run_converge(args):
 
 
 def run_phases(args):
-    """One launch per pass kind on 512 lattices of the benchmark workload, so an
-    ncu capture (-k regex:llr_kernel) sees: resync, approach, overrelaxation
-    pass, heat-bath pass, composite sweep."""
+    """One launch per pass kind on 456 lattices of the benchmark workload (one
+    full wave of 256-thread CTAs: 3 per SM on 152 SMs), so an ncu capture
+    (-k regex:llr_kernel) sees: resync, approach, overrelaxation pass,
+    heat-bath pass, composite sweep."""
     import torch
     torch.cuda.set_device(0)
     from paper_1509_08391_gb300 import build as bld
     bld.build()
     from paper_1509_08391_gb300 import llr, workloads
-    w = workloads.subset(workloads.l20_critical(), range(512))
+    w = workloads.subset(workloads.l20_critical(), range(456))
     with llr.Batch.from_workload(w, max_approach=1000) as b:
         b.set_kernel_config(args.threads or 256, True)
         a = np.full(w.n_lattices, -1.01)
