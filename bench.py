@@ -27,9 +27,8 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "link updates/s"
-SFU_OPS_PER_CLK_SM = 16          # sin/cos special-function throughput per SM per clock
-SINCOS_PER_UPDATE = 8            # 6 staples + old and new link angle
-MUFU_PER_SINCOS = 2              # one sine and one cosine
+SFU_OPS_PER_CLK_SM = 16          # special-function (MUFU) ops per SM per clock
+MUFU_PER_UPDATE = 12             # algorithmic: sine and cosine of the 6 staple angles
 BYTES_PER_UPDATE = 8             # algorithmic: read + write one float32 link
 
 
@@ -307,8 +306,8 @@ def run_ours(args, rank, world, local_rank):
     # roofline of the dominant kernel (the batched sweep kernel, one launch per step)
     upd_per_launch = upd_per_step
     mhz = clk.get("sm_max_mhz") or 2070.0
-    peak_sfu = SFU_OPS_PER_CLK_SM * 152 * mhz * 1e6 / MUFU_PER_SINCOS / 1e9   # Gsincos/s
-    ach_sfu = SINCOS_PER_UPDATE * upd_per_launch / (per_launch_ms / 1e3) / 1e9
+    peak_sfu = SFU_OPS_PER_CLK_SM * 152 * mhz * 1e6 / 1e9               # G MUFU ops/s
+    ach_sfu = MUFU_PER_UPDATE * upd_per_launch / (per_launch_ms / 1e3) / 1e9
     hbm_peak = 6802.0
     try:
         hbm_peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
@@ -326,10 +325,11 @@ def run_ours(args, rank, world, local_rank):
         "acceptance": {"heat_bath": hb, "overrelaxation": orr},
         "max_tracked_minus_fresh": drift, "status_ok": status_ok,
         "roofline": {"bound": "alu", "achieved": ach_sfu, "peak": peak_sfu,
-                     "unit": "Gsincos/s (SFU pipe)", "frac": ach_sfu / peak_sfu,
+                     "unit": "G MUFU ops/s (SFU pipe)", "frac": ach_sfu / peak_sfu,
                      "traffic": traffic,
-                     "peak_source": "16 SFU ops/clk/SM x 152 SMs x %.0f MHz / 2 ops per "
-                                    "sincos (derived)" % mhz},
+                     "algorithmic": "12 MUFU ops per link update (sine and cosine of 6 staples)",
+                     "peak_source": "16 MUFU ops/clk/SM x 152 SMs x %.0f MHz (derived from "
+                                    "unit counts and the sampled max clock)" % mhz},
         "roofline_hbm": {"bound": "hbm", "achieved": ach_hbm, "peak": hbm_peak, "unit": "GB/s",
                          "frac": ach_hbm / hbm_peak, "peak_source": "MEASURED_PEAKS.json"},
         "clocks": clk, "gpu_launches": args.steps,
