@@ -51,6 +51,14 @@ def parse():
     p.add_argument("--target-intervals", type=int, default=32)
     p.add_argument("--target-replicas", type=int, default=4)
     p.add_argument("--n-rm", type=int, default=150)
+    p.add_argument("--physics", action="store_true",
+                   help="the paper's volume study at one L (Tab. SimDet parameters): "
+                        "beta_c(L) and the specific-heat peak against Tab. peakloc / Tab. peak")
+    p.add_argument("--phys-L", type=int, default=8)
+    p.add_argument("--phys-replicas", type=int, default=8)
+    p.add_argument("--phys-therm", type=int, default=5)
+    p.add_argument("--phys-meas", type=int, default=20)
+    p.add_argument("--phys-rm", type=int, default=0, help="0 = the paper's N_RM")
     p.add_argument("--phases", action="store_true",
                    help="profiling driver: one overrelaxation pass, one heat-bath pass and one "
                         "composite sweep of 456 lattices of the workload (for ncu)")
@@ -408,6 +416,83 @@ def run_converge(args):
     print(json.dumps(out), flush=True)
 
 
+# The paper's results for the volume study (Tab. peakloc, Tab. peak): beta_c(L)
+# and the specific-heat peak, normalised as var(E/6V) (its "C_V/(6V)").
+PAPER_BETA_C = {8: (1.00744, 2e-5), 10: (1.00939, 2e-5), 12: (1.010245, 1e-6),
+                14: (1.010635, 5e-6), 16: (1.010833, 4e-6), 18: (1.010948, 2e-6),
+                20: (1.011006, 2e-6)}
+PAPER_CV_PEAK = {8: (0.000551, 2e-6), 10: (0.000384, 2e-6), 12: (0.0002971, 1.1e-6),
+                 14: (0.0002537, 8e-7), 16: (0.0002272, 7e-7), 18: (0.0002097, 5e-7),
+                 20: (0.0002007, 4e-7)}
+
+
+def physics_study(L, replicas, n_therm, n_meas, n_rm, beta_window=(1.0, 1.016)):
+    """The whole LLR path at the paper's volume-study parameters: hot start,
+    approach, n_rm graph-replayed Robbins-Monro iterations of every
+    (interval, replica) chain from a = -1, then per replica ln rho and the
+    specific-heat peak; returns the per-replica beta_c and var(E/6V) peak."""
+    import torch
+    from paper_1509_08391_gb300 import llr, workloads
+    w = workloads.paper_volume_study(L, replicas, n_therm, n_meas, n_rm)
+    n = w.n_lattices
+    stream = torch.cuda.Stream()
+    t_all = time.perf_counter()
+    with llr.Batch.from_workload(w, stream=stream.cuda_stream, max_approach=5000) as b:
+        a_dev = torch.full((n,), w.a0, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.rm_run(a_dev, w.n_therm, w.n_meas, 0, w.n_rm)
+        torch.cuda.synchronize()
+        t_rm = time.perf_counter() - t0
+        a = a_dev.cpu().numpy()
+        ok = bool(np.all(b.status() == 0))
+        st = b.stats()
+    six_v = 6.0 * L ** 4
+    lo = np.asarray(w.E_lo)
+    rid = np.asarray(w.replica_id)
+    iid = np.asarray(w.interval_id)
+    dE = w.dE[0]
+    bc, cv = [], []
+    for r in range(replicas):
+        idx = np.where(rid == r)[0]
+        idx = idx[np.argsort(iid[idx])]
+        c = lo[idx] + 0.5 * dE
+        b_r, v_r = llr.cv_peak(c, a[idx], beta_window[0], beta_window[1], n_grid=1601, tol=1e-10)
+        bc.append(b_r)
+        cv.append(v_r / six_v ** 2)
+    upd = n * w.n_rm * (w.n_therm + w.n_meas) * (1 + w.n_or) * 4 * L ** 4
+    return {"workload": w.name, "L": L, "intervals": 512, "replicas": replicas, "dE": dE,
+            "E_over_6V": [lo.min() / six_v, (lo.max() + dE) / six_v],
+            "n_therm": w.n_therm, "n_meas": w.n_meas, "n_rm": w.n_rm, "a0": w.a0,
+            "status_ok": ok, "heat_bath_acceptance": float(st["hb_acc"].sum() / st["hb_tot"].sum()),
+            "beta_c_per_replica": bc, "cv_peak_per_replica": cv,
+            "rm_seconds": t_rm, "wall_seconds": time.perf_counter() - t_all,
+            "link_updates_per_s": upd / t_rm}
+
+
+def run_physics(args):
+    """--physics: beta_c(L) and the specific-heat peak of the paper's volume
+    study, computed end to end on the GPU, against the paper's tables."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1509_08391_gb300 import build as bld
+    bld.build()
+    L = args.phys_L
+    res = physics_study(L, args.phys_replicas, args.phys_therm, args.phys_meas, args.phys_rm)
+    R = len(res["beta_c_per_replica"])
+    for key, paper in (("beta_c", PAPER_BETA_C), ("cv_peak", PAPER_CV_PEAK)):
+        v = np.asarray(res[key + "_per_replica"])
+        m, e = float(v.mean()), float(v.std(ddof=1) / np.sqrt(R)) if R > 1 else float("nan")
+        res[key] = {"mean": m, "stderr": e}
+        if L in paper:
+            pv, pe = paper[L]
+            res[key]["paper"] = pv
+            res[key]["paper_err"] = pe
+            res[key]["deviation_sigma"] = (m - pv) / float(np.hypot(e, pe))
+    res["metric"] = "beta_c(L) and C_V peak vs the paper (Tab. peakloc, Tab. peak)"
+    print(json.dumps(res), flush=True)
+
+
 def run_phases(args):
     """One launch per pass kind on 456 lattices of the benchmark workload (one
     full wave of 256-thread CTAs: 3 per SM on 152 SMs), so an ncu capture
@@ -436,6 +521,9 @@ def main():
         return
     if args.converge:
         run_converge(args)
+        return
+    if args.physics:
+        run_physics(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

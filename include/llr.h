@@ -130,6 +130,24 @@ int llr_rm_run(llr_handle h, int n_therm, int n_meas, int rm_index0, int n_steps
 int llr_rm_step_plain(llr_handle h, int n_therm, int n_meas, int rm_index, double *a_inout,
                       double *dE_mean_out);
 
+/* One round of replica exchange between overlapping intervals (Sec. 2.5).
+ * For each pair (I1, I2) = (pairs[2k], pairs[2k+1]) of lattice indices: if
+ * the tracked energies of both current configurations lie in the common part
+ * of the two closed windows, the configurations are exchanged with the
+ * Metropolis probability min(1, exp((a[I1] - a[I2]) (E_C1 - E_C2))).  The
+ * decision uses a 53-bit uniform from Philox keyed by I1's key, counter
+ * (0, round, 13, 0); pass a different round to every call.  An exchange
+ * moves the link angles and the tracked energy; the window, slope, Philox
+ * key, sweep counter and statistics stay with the lattice index.
+ *   pairs: host int[2 n_pairs]; every lattice appears at most once and both
+ *     lattices of a pair have the same L.  a: host double[n_lattices], the
+ *     current slopes a^(n).  accepted_out: host int[n_pairs] (1 = exchanged)
+ *     or NULL.  Synchronous.
+ * Errors: LLR_ERR_ARG for an index out of range, a repeated lattice, pairs
+ * of different L, n_pairs < 0 or > n_lattices / 2, or a non-finite slope. */
+int llr_replica_exchange(llr_handle h, int n_pairs, const int *pairs, const double *a,
+                         uint32_t round, int *accepted_out);
+
 /* Fresh energies E = sum_P cos(theta_P) of every lattice, accumulated in
  * FP64 from the float32 angles (Sec. 3.1).  E_out: host double[n_lattices]. */
 int llr_energy(llr_handle h, double *E_out);
@@ -264,7 +282,8 @@ int llr_set_wait_limit(llr_handle h, unsigned long long ns);
  * tracked energies, sweep counters, slopes, statistics) fits in
  * llr_state_bytes(h) bytes; llr_save_state copies it to the host buffer
  * `out`, llr_load_state copies it back into a handle created with the same
- * configuration (checked: LLR_ERR_ARG otherwise).  Random numbers are keyed
+ * configuration (checked: LLR_ERR_ARG otherwise; the arrangement of link
+ * arrays that replica exchanges produced is part of the state).  Random numbers are keyed
  * by the sweep counter, so a resumed run continues bit-identically. */
 size_t llr_state_bytes(llr_handle h);
 int llr_save_state(llr_handle h, void *out);

@@ -84,6 +84,7 @@ def lib():
                 "orc_batch_run": (I, [P, I, U64, ip, ip, dp, dp, dp, dp, I, I, I, I, I, I, I,
                                       D, D, I, ip, dp]),
                 "orc_batch_sweeps": (None, [P, dp, I, I, I]),
+                "orc_replica_exchange": (I, [P, I, ip, dp, U32, ip]),
                 "orc_batch_approach": (None, [P, ip, I, I, I]),
             }
             for name, (res, args) in sig.items():
@@ -283,6 +284,19 @@ def parallel_sweeps(lattices, a, n_sweeps, n_threads):
     av = np.ascontiguousarray(np.broadcast_to(a, (n,)), dtype=np.float64)
     lib().orc_batch_sweeps(ctypes.cast(arr, ctypes.c_void_p), _dp(av), n, int(n_sweeps),
                            int(n_threads))
+
+
+def replica_exchange(lattices, pairs, a, round_):
+    """One replica-exchange round over the given pairs of lattices of
+    overlapping intervals (Sec. 2.5).  Returns the accepted flags."""
+    n = len(lattices)
+    arr = (ctypes.c_void_p * n)(*[t._h for t in lattices])
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1)
+    av = np.ascontiguousarray(np.broadcast_to(a, (n,)), dtype=np.float64)
+    acc = np.zeros(max(len(pr) // 2, 1), dtype=np.int32)
+    lib().orc_replica_exchange(ctypes.cast(arr, ctypes.c_void_p), len(pr) // 2, _ip(pr), _dp(av),
+                               int(round_) & 0xFFFFFFFF, _ip(acc))
+    return acc[:len(pr) // 2].astype(bool)
 
 
 def parallel_approach(lattices, max_sweeps, n_threads):

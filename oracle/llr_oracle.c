@@ -57,6 +57,10 @@
  *      energy lies in the window at the end of a composite sweep.
  *   R6 the tracked energy is re-synchronised with a fresh plaquette sum at
  *      the end of every composite sweep; the measurement uses that value.
+ *   R7 replica exchange (Sec. 2.5): the caller names the pairs of overlapping
+ *      intervals tried in one exchange round and a round number; the draw
+ *      deciding a pair comes from Philox keyed by the pair's first lattice,
+ *      counter (0, round, swap tag, 0), as a 53-bit uniform in [0, 1).
  */
 #include <math.h>
 #include <stdint.h>
@@ -255,6 +259,7 @@ typedef struct {
 } orc_lat;
 
 #define TAG_HB 0u
+#define TAG_SWAP 13u
 #define TAG_APPROACH 14u
 #define TAG_INIT 15u
 #define SAMPLER_MAX_ATTEMPTS 64
@@ -591,6 +596,44 @@ double orc_lat_rm_step(orc_lat *t, double a, int n_therm, int n_meas, int rm_ind
     double mean = n_meas > 0 ? sum / n_meas : 0.0;
     if (mean_out) *mean_out = mean;
     return a + 12.0 * mean / (t->dE * t->dE * (double)(rm_index + 1));
+}
+
+/* Replica exchange between overlapping intervals (Sec. 2.5).  For each pair
+ * (I1, I2) = (pairs[2k], pairs[2k+1]), in order: when the current energies
+ * E1, E2 of both configurations lie in the common part of the two closed
+ * windows, the configurations are exchanged with probability
+ * min(1, exp((a_I1 - a_I2)(E1 - E2))), the Metropolis probability of the
+ * swap under the product of the two restricted weights exp(-a E).  An
+ * exchange moves the link angles and the tracked energy; the window, the
+ * slope, the Philox key and the sweep counter stay with the interval.
+ * a: slopes a^(n) indexed like lats.  accepted (nullable): 1 per exchanged
+ * pair.  Returns the number of exchanges. */
+int orc_replica_exchange(orc_lat **lats, int n_pairs, const int *pairs, const double *a,
+                         uint32_t round, int *accepted)
+{
+    int n_acc = 0;
+    for (int k = 0; k < n_pairs; ++k) {
+        int i1 = pairs[2 * k], i2 = pairs[2 * k + 1];
+        orc_lat *t1 = lats[i1], *t2 = lats[i2];
+        double lo = fmax(t1->E_lo, t2->E_lo);
+        double hi = fmin(t1->E_lo + t1->dE, t2->E_lo + t2->dE);
+        int acc = 0;
+        if (t1->E >= lo && t1->E <= hi && t2->E >= lo && t2->E <= hi) {
+            double x = (a[i1] - a[i2]) * (t1->E - t2->E);
+            uint32_t ctr[4] = {0u, round, TAG_SWAP, 0u}, w[4];
+            orc_philox4x32_10(ctr, t1->key, w);
+            double u = ((double)(w[0] >> 11) * 4294967296.0 + (double)w[1]) *
+                       (1.0 / 9007199254740992.0);
+            acc = x >= 0.0 || u < exp(x);
+        }
+        if (acc) {
+            double *th = t1->theta; t1->theta = t2->theta; t2->theta = th;
+            double E = t1->E; t1->E = t2->E; t2->E = E;
+        }
+        if (accepted) accepted[k] = acc;
+        n_acc += acc;
+    }
+    return n_acc;
 }
 
 /* Per-link staple modulus |S| and angle alpha (for invariance checks). */

@@ -2,11 +2,13 @@
 // checking, device allocation of the lattice batch, stream-ordered launches
 // and host <-> device marshalling.  All arithmetic of the method runs in the
 // kernels of llr_chain.cu and llr_recon.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/llr.h"
@@ -34,6 +36,7 @@ struct llr_ctx {
     unsigned *d_sync = nullptr;      // work queue of the persistent kernel: 2 + n words
     int *d_order = nullptr;          // 0 .. n-1 (single-lattice launches point into it)
     int *d_step = nullptr;           // Robbins-Monro step counter of graph replays
+    int *d_pairs = nullptr;          // replica-exchange pairs (n ints: at most n/2 pairs)
     // one captured Robbins-Monro step (memset, persistent kernel, step + 1)
     cudaGraphExec_t rm_graph = nullptr;
     int g_therm = -1, g_meas = -1, g_index0 = -1;
@@ -410,6 +413,41 @@ int llr_rm_step_plain(llr_handle h, int n_therm, int n_meas, int rm_index, doubl
     return LLR_OK;
 }
 
+int llr_replica_exchange(llr_handle h, int n_pairs, const int *pairs, const double *a_host,
+                         uint32_t round, int *accepted_out)
+{
+    if (int r = check_handle(h)) return r;
+    if (n_pairs < 0 || 2ll * n_pairs > (long long)h->n)
+        return fail(LLR_ERR_ARG, "n_pairs must be in [0, n_lattices / 2]");
+    if (n_pairs == 0) return LLR_OK;
+    if (!pairs || !a_host) return fail(LLR_ERR_ARG, "null pairs or a");
+    std::vector<char> used((size_t)h->n, 0);
+    for (int k = 0; k < 2 * n_pairs; ++k) {
+        const int i = pairs[k];
+        if (i < 0 || i >= h->n) return fail(LLR_ERR_ARG, "pair index out of range");
+        if (used[(size_t)i]) return fail(LLR_ERR_ARG, "lattice " + std::to_string(i) +
+                                                          " appears in two pairs");
+        used[(size_t)i] = 1;
+    }
+    for (int k = 0; k < n_pairs; ++k)
+        if (h->h_lat[(size_t)pairs[2 * k]].L != h->h_lat[(size_t)pairs[2 * k + 1]].L)
+            return fail(LLR_ERR_ARG, "the lattices of a pair must have the same L");
+    for (int i = 0; i < h->n; ++i)
+        if (!std::isfinite(a_host[i])) return fail(LLR_ERR_ARG, "non-finite a");
+    if (!h->d_pairs) LLR_CUDA(cudaMalloc(&h->d_pairs, sizeof(int) * (size_t)h->n));
+    LLR_CUDA(cudaMemcpyAsync(h->d_pairs, pairs, sizeof(int) * 2 * (size_t)n_pairs,
+                             cudaMemcpyHostToDevice, h->stream));
+    LLR_CUDA(cudaMemcpyAsync(h->d_a, a_host, sizeof(double) * (size_t)h->n,
+                             cudaMemcpyHostToDevice, h->stream));
+    LLR_CUDA(llr::launch_replica_exchange(h->d_lat, h->d_pairs, n_pairs, h->d_a, round, h->d_int,
+                                          h->stream));
+    if (accepted_out)
+        LLR_CUDA(cudaMemcpyAsync(accepted_out, h->d_int, sizeof(int) * (size_t)n_pairs,
+                                 cudaMemcpyDeviceToHost, h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    return LLR_OK;
+}
+
 int llr_energy(llr_handle h, double *E_out)
 {
     if (int r = check_handle(h)) return r;
@@ -563,13 +601,21 @@ int llr_load_state(llr_handle h, const void *in)
     if (int r = check_handle(h)) return r;
     if (!in) return fail(LLR_ERR_ARG, "null buffer");
     const LatState *st = (const LatState *)in;
+    // replica exchange moves link arrays between lattices of the same L, so a
+    // saved state may hold any arrangement of this handle's arrays among them
+    std::vector<std::pair<unsigned long long, int>> own((size_t)h->n), saved((size_t)h->n);
     for (int i = 0; i < h->n; ++i) {
         const LatState &a = st[i], &b = h->h_lat[(size_t)i];
-        if (a.L != b.L || a.half != b.half || a.off != b.off || a.key0 != b.key0 ||
-            a.key1 != b.key1 || a.lo_fx != b.lo_fx || a.hi_fx != b.hi_fx)
+        if (a.L != b.L || a.half != b.half || a.key0 != b.key0 || a.key1 != b.key1 ||
+            a.lo_fx != b.lo_fx || a.hi_fx != b.hi_fx)
             return fail(LLR_ERR_ARG, "state of lattice " + std::to_string(i) +
                                          " was saved from a different configuration");
+        own[(size_t)i] = {b.off, b.L};
+        saved[(size_t)i] = {a.off, a.L};
     }
+    std::sort(own.begin(), own.end());
+    std::sort(saved.begin(), saved.end());
+    if (own != saved) return fail(LLR_ERR_ARG, "saved link arrays do not match this handle");
     LLR_CUDA(cudaMemcpyAsync(h->d_lat, in, sizeof(LatState) * (size_t)h->n, cudaMemcpyHostToDevice,
                              h->stream));
     LLR_CUDA(cudaMemcpyAsync(h->d_theta, (const char *)in + sizeof(LatState) * (size_t)h->n,
@@ -592,6 +638,7 @@ int llr_destroy(llr_handle h)
     cudaFree(h->d_sync);
     cudaFree(h->d_order);
     cudaFree(h->d_step);
+    cudaFree(h->d_pairs);
     if (h->rm_graph) cudaGraphExecDestroy(h->rm_graph);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     delete h;

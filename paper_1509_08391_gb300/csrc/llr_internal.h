@@ -81,6 +81,12 @@ cudaError_t launch_to_canonical(const LatState *lat_dev, const float *theta, flo
 cudaError_t launch_from_canonical(const LatState *lat_dev, float *theta, const float *in,
                                   int n_links, cudaStream_t s);
 
+// One replica-exchange round over disjoint pairs of lattices (device arrays:
+// pairs int[2 n_pairs], a double[n_lat], accepted int[n_pairs] or null).
+cudaError_t launch_replica_exchange(LatState *lats, const int *pairs, int n_pairs,
+                                    const double *a, uint32_t round, int *accepted,
+                                    cudaStream_t s);
+
 // Record the message returned by llr_last_error() on this thread; returns code.
 int set_last_error(int code, const char *msg);
 

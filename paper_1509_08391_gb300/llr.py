@@ -31,7 +31,7 @@ EXPORTS = [
     "llr_mlp_create", "llr_mlp_num_params", "llr_mlp_get_params", "llr_mlp_set_params",
     "llr_mlp_set_norm", "llr_mlp_get_norm", "llr_mlp_predict", "llr_mlp_grad", "llr_mlp_fit",
     "llr_mlp_destroy", "llr_set_wait_limit", "llr_state_bytes", "llr_save_state",
-    "llr_load_state",
+    "llr_load_state", "llr_replica_exchange",
 ]
 NOALLOC_MAX_CENTRES = 65536
 
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
         "llr_set_wait_limit": [P, ctypes.c_ulonglong],
         "llr_save_state": [P, P],
         "llr_load_state": [P, P],
+        "llr_replica_exchange": [P, I, P, P, U32, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -230,6 +231,16 @@ class Batch:
         _check(load().llr_rm_step_plain(self._h, int(n_therm), int(n_meas), int(rm_index),
                                         _ptr(a), _ptr(mean)))
         return a, mean
+
+    def replica_exchange(self, pairs, a, round_):
+        """One replica-exchange round over pairs of lattices of overlapping
+        intervals (llr_replica_exchange); returns the exchanged flags."""
+        pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1)
+        a = np.ascontiguousarray(np.broadcast_to(a, (self.n,)), dtype=np.float64)
+        acc = np.zeros(max(pr.size // 2, 1), dtype=np.int32)
+        _check(load().llr_replica_exchange(self._h, pr.size // 2, _ptr(pr), _ptr(a),
+                                           int(round_) & 0xFFFFFFFF, _ptr(acc)))
+        return acc[:pr.size // 2].astype(bool)
 
     # ------------------------------------------------------------ inspection
     def energy(self):

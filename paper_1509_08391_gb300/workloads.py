@@ -111,6 +111,32 @@ def warm_start_targets(L: int, replicas: int = 4, n_int: int = 128) -> Workload:
                  SEED_BASE + 4, n_therm=10, n_meas=40, n_rm=100)
 
 
+def overlapping_l4(replicas: int = 2, n_int: int = 6) -> Workload:
+    """L=4 with overlapping windows for replica exchange (Sec. 2.5): n_int
+    windows of width dE = 16 whose lower edges are 8 apart (half overlap),
+    starting at E/6V = 0.58."""
+    L, dE = 4, 16.0
+    six_v = 6.0 * L ** 4
+    e_hi = (0.58 * six_v + 8.0 * (n_int - 1) + dE) / six_v
+    return _grid("u1_4d_L4_%dint_overlap" % n_int, [L], n_int, 0.58, e_hi, [dE], replicas,
+                 SEED_BASE + 5, n_therm=5, n_meas=20, n_rm=20)
+
+
+def exchange_pairs(w: Workload, parity: int):
+    """The lattice pairs tried in one replica-exchange round: neighbouring
+    windows (k, k+1) with k = parity mod 2, same L and same replica, in
+    ascending order of the window edge.  Index bookkeeping only."""
+    by_key = {}
+    for i in range(w.n_lattices):
+        by_key.setdefault((w.L[i], w.replica_id[i]), []).append(i)
+    pairs = []
+    for key in sorted(by_key):
+        idx = sorted(by_key[key], key=lambda i: w.E_lo[i])
+        for k in range(parity & 1, len(idx) - 1, 2):
+            pairs.append((idx[k], idx[k + 1]))
+    return pairs
+
+
 def subset(w: Workload, idx) -> Workload:
     idx = list(idx)
     pick = lambda xs: [xs[i] for i in idx]
@@ -118,3 +144,32 @@ def subset(w: Workload, idx) -> Workload:
                     pick(w.interval_id), pick(w.replica_id), w.seed, w.n_or, w.block,
                     w.n_therm, w.n_meas, w.n_rm, w.a0, w.beta_up, w.beta_dn, w.max_approach,
                     dict(w.notes))
+
+
+# Energy ranges of the paper's volume study (Tab. SimDet): E/6V from E_min
+# to E_max in 512 contiguous intervals; N_SW sweeps and N_RM Robbins-Monro
+# iterations per interval.
+PAPER_VOLUME_STUDY = {
+    8: (0.5722222, 0.67, 250, 600),
+    10: (0.59, 0.687777, 200, 400),
+    12: (0.59, 0.687777, 200, 400),
+    14: (0.59, 0.687777, 200, 400),
+    16: (0.59, 0.687777, 200, 400),
+    18: (0.59, 0.687777, 200, 400),
+    20: (0.59, 0.687777, 200, 400),
+}
+
+
+def paper_volume_study(L: int, replicas: int = 8, n_therm: int = 5, n_meas: int = 20,
+                       n_rm: int = 0) -> Workload:
+    """The paper's L^4 study (Tab. SimDet): 512 contiguous intervals of width
+    dE = (E_max - E_min) / 512 over its E/6V range, `replicas` independent
+    chains per interval (the paper repeats each run N_B = 20 times), N_RM
+    Robbins-Monro iterations (the paper's value when n_rm = 0).  Sweeps per
+    iteration are composite sweeps (1 heat-bath + 4 overrelaxation passes)."""
+    e_lo, e_hi, _n_sw, n_rm_paper = PAPER_VOLUME_STUDY[L]
+    n_int = 512
+    dE = 6.0 * L ** 4 * (e_hi - e_lo) / n_int
+    return _grid("u1_4d_L%d_512int_x%d_paper" % (L, replicas), [L], n_int, e_lo, e_hi, [dE],
+                 replicas, SEED_BASE + 10 + L, n_therm=n_therm, n_meas=n_meas,
+                 n_rm=n_rm if n_rm > 0 else n_rm_paper)
