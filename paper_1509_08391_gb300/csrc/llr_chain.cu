@@ -108,11 +108,11 @@ __device__ __forceinline__ bool von_mises(float kappa, uint32_t c0, uint32_t c1,
     // ... then evaluate the accepted variate once, accurately
     const float u1 = u01(w_acc);
     float sh, ch;
-    sincospif(0.5f * u1, &sh, &ch);
+    __sincosf(0.5f * kPi * u1, &sh, &ch);
     const float z = (ch - sh) * (ch + sh);
     const float den = r + z;
     const bool pos = 1.0f + r * z >= 0.0f;                   // f >= 0
-    const float w = (pos ? rm1 * 2.0f * sh * sh : (r + 1.0f) * 2.0f * ch * ch) / den;
+    const float w = __fdividef(pos ? rm1 * 2.0f * sh * sh : (r + 1.0f) * 2.0f * ch * ch, den);
     const float s = sqrtf(fmaxf(w * (2.0f - w), 0.0f));
     const float c = pos ? 1.0f - w : w - 1.0f;
     const bool neg_x = !(w_acc & 1u);                        // X = -acos f
@@ -152,10 +152,11 @@ __device__ __forceinline__ int decode_half(int h, int p, int L, uint32_t magic, 
 // backward phi = theta_nu(x-nu) - theta_nu(x-nu+mu) - theta_mu(x-nu)
 // so that the link's local energy is sum_j cos(theta + phi_j) = Re(e^{i theta} S).
 //
-// The 18 neighbour angles are staged through shared memory: staple_fetch
-// issues one 4-byte asynchronous copy (cp.async, cached in L1) per angle into
-// the calling thread's column of a stage buffer, staple_from sums the staples
-// from it once the copies have landed.  A thread only reads what it copied
+// In a heat-bath pass the 18 neighbour angles are staged through shared
+// memory: staple_fetch issues one 4-byte asynchronous copy (cp.async, cached
+// in L1) per angle into the calling thread's column of a stage buffer, and
+// staple_from sums the staples from it once the copies have landed, so a
+// producer's loads for its next link overlap the sampling of the current one.  A thread only reads what it copied
 // itself, so cp.async.wait_group is the only synchronisation.  The copies
 // read through L1 like plain loads: other classes of this lattice were
 // written earlier in the same launch (same CTA, or another CTA before the
@@ -377,11 +378,64 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, float *th, int p, floa
     if (lane == 0) atomicAdd(&sm.acc_cnt, (unsigned long long)cnt);
 }
 
-// One overrelaxation class (MU, p): theta' = -theta - 2 alpha keeps
-// |S| cos(theta + alpha), so E is unchanged in exact arithmetic and the move
-// is always inside the window; every link is written directly by every warp
-// (the float32 rounding of E, ~1e-6 per link, is absorbed by the resync at
-// the end of the composite sweep).
+// Neighbour angles of link theta_MU(x) (site s, parity p) loaded straight into
+// registers v[18], in the order of staple_fetch.
+template <int MU>
+__device__ __forceinline__ void staple_load(const float *th, int half, int L, const int x[4],
+                                            int s, int p, float v[18])
+{
+    const int st[4] = {1, L, L * L, L * L * L};
+    const int dmu = (x[MU] == L - 1) ? -(L - 1) * st[MU] : st[MU];
+    const int spmu = s + dmu;
+    const int q = p ^ 1;
+    const float *thmu_q = th + (2 * MU + q) * half;
+    int j = 0;
+#pragma unroll
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == MU) continue;
+        const int dnf = (x[nu] == L - 1) ? -(L - 1) * st[nu] : st[nu];
+        const int dnb = (x[nu] == 0) ? (L - 1) * st[nu] : -st[nu];
+        const int spnu = s + dnf;
+        const int smnu = s + dnb;
+        const int smnu_pmu = smnu + dmu;
+        const float *thnu_p = th + (2 * nu + p) * half;
+        const float *thnu_q = th + (2 * nu + q) * half;
+        v[6 * j + 0] = thnu_q[spmu >> 1];
+        v[6 * j + 1] = thmu_q[spnu >> 1];
+        v[6 * j + 2] = thnu_p[s >> 1];
+        v[6 * j + 3] = thnu_p[smnu_pmu >> 1];
+        v[6 * j + 4] = thmu_q[smnu >> 1];
+        v[6 * j + 5] = thnu_q[smnu >> 1];
+        ++j;
+    }
+}
+
+// Overrelaxation of one link from its 18 neighbour angles: the staples are
+// formed exactly as in staple_from, theta' = -theta - 2 alpha, alpha = arg S.
+template <bool FAST>
+__device__ __forceinline__ float reflect_from(const float v[18], float t0)
+{
+    float Sr = 0.0f, Si = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float pf = v[6 * j] - v[6 * j + 1] - v[6 * j + 2];
+        const float pb = v[6 * j + 5] - v[6 * j + 3] - v[6 * j + 4];
+        float sf, cf, sb, cb;
+        sin_cos<FAST>(pf, &sf, &cf);
+        sin_cos<FAST>(pb, &sb, &cb);
+        Sr += cf + cb;
+        Si += sf + sb;
+    }
+    return wrap_angle(-t0 - 2.0f * atan2f(Si, Sr));
+}
+
+// One overrelaxation group: the links of class (MU, p) with half-site index
+// in [h0, h0 + count).  theta' = -theta - 2 alpha keeps |S| cos(theta + alpha),
+// so E is unchanged in exact arithmetic and the move is always inside the
+// window; every link is written directly (the float32 rounding of E, ~1e-6
+// per link, is absorbed by the resync at the end of the composite sweep).
+// The neighbours are plain loads: within a slab they mostly hit L1/L2, and
+// with no consumer to feed the loads of many warps hide each other.
 template <int MU, int NWP, bool FAST>
 __device__ __noinline__ void overrelax_class(Smem<NWP> &sm, float *th, int p, int h0, int count)
 {
@@ -390,34 +444,14 @@ __device__ __noinline__ void overrelax_class(Smem<NWP> &sm, float *th, int p, in
     const uint32_t magic = sm.st.magic;
     float *own = th + (2 * MU + p) * half;
     const int tid = threadIdx.x;
-    bool valid_n = tid < count;
-    float t0_n = 0.0f;
-    if (valid_n) {
+    for (int local = tid; local < count; local += NT) {
+        float va[18];
         int x[4];
-        const int site = decode_half(h0 + tid, p, L, magic, x);
-        staple_fetch<MU>(th, half, L, x, site, p, stage_col<NT>(0), NT);
-        t0_n = own[h0 + tid];
+        const int site = decode_half(h0 + local, p, L, magic, x);
+        staple_load<MU>(th, half, L, x, site, p, va);
+        const float ta = own[h0 + local];
+        own[h0 + local] = reflect_from<FAST>(va, ta);
     }
-    cp_async_commit();
-    for (int it = 0, local = tid; local < count; ++it, local += NT) {
-        const float t0 = t0_n;
-        {
-            const int ln = local + NT;
-            valid_n = ln < count;
-            if (valid_n) {
-                int x[4];
-                const int site = decode_half(h0 + ln, p, L, magic, x);
-                staple_fetch<MU>(th, half, L, x, site, p, stage_col<NT>((it + 1) & 1), NT);
-                t0_n = own[h0 + ln];
-            }
-            cp_async_commit();
-        }
-        cp_async_wait<1>();
-        float Sr, Si;
-        staple_from<FAST>(stage_col<NT>(it & 1), NT, Sr, Si);
-        own[h0 + local] = wrap_angle(-t0 - 2.0f * atan2f(Si, Sr));
-    }
-    cp_async_wait<0>();
 }
 
 // Consumer side: sequential Metropolis accept of the chunk's blocks in link

@@ -73,13 +73,14 @@ def slopes_by_interval(w: workloads.Workload, a_lat):
 
 
 def training_set(n_int=24, replicas=2, n_rm=40, n_therm=2, n_meas=8, seed=None, stream=None,
-                 Ls=(8, 10, 12, 14, 16)):
-    """The method's own slopes at small volumes (one uneven batch)."""
+                 Ls=(8, 10, 12, 14, 16), e_lo=0.58, e_hi=0.68):
+    """The method's own slopes at small volumes (one uneven batch) for
+    intervals over E/6V in [e_lo, e_hi]."""
     base = workloads.uneven_batch()
     L, lo, de, iid, rid = [], [], [], [], []
     for g, Lg in enumerate(Ls):
         dE = 8.0 * (Lg / 8) ** 2
-        E = workloads.place_intervals(Lg, n_int, 0.58, 0.68, dE)
+        E = workloads.place_intervals(Lg, n_int, e_lo, e_hi, dE)
         for k in range(n_int):
             for r in range(replicas):
                 L.append(Lg)

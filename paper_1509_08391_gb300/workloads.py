@@ -103,11 +103,13 @@ def l20_critical(replicas: int = 8, n_int: int = 256) -> Workload:
                  SEED_BASE + 3, n_therm=10, n_meas=40, n_rm=200)
 
 
-def warm_start_targets(L: int, replicas: int = 4, n_int: int = 128) -> Workload:
+def warm_start_targets(L: int, replicas: int = 4, n_int: int = 128, e_lo: float = 0.58,
+                       e_hi: float = 0.68) -> Workload:
     """Prediction targets of the learned warm start: 128 intervals over
-    E/6V in [0.58, 0.68] at L = 20 or 24, dE scaled with sqrt(V)."""
+    E/6V in [e_lo, e_hi] (default [0.58, 0.68]) at L = 20 or 24, dE scaled
+    with sqrt(V)."""
     dE = 8.0 * (L / 8) ** 2
-    return _grid("u1_4d_L%d_128int_warm" % L, [L], n_int, 0.58, 0.68, [dE], replicas,
+    return _grid("u1_4d_L%d_%dint_warm" % (L, n_int), [L], n_int, e_lo, e_hi, [dE], replicas,
                  SEED_BASE + 4, n_therm=10, n_meas=40, n_rm=100)
 
 

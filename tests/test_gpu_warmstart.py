@@ -1,14 +1,15 @@
 """What the learned warm start gains over the method without it (small volumes).
 
 Training data are the method's own slopes at L = 8 ... 16 from a short
-uneven-batch run; the network predicts the slopes at L = 20 and starts the
-Robbins-Monro iteration there with the gain offset n0.  Compared with the
-naive start a = -1, n0 = 0 (Sec. 2.4 allows either): the predicted start is
-closer to the long reference run, it stays closer over the first steps, and
-the warm-started slopes still agree with the reference within 3 sigma.  The
-energy range sits at the transition, where the slopes are close to -1, so the
-naive start is itself within ~0.01-0.02 of the reference: the test asks for
-"closer", not for a fixed factor.
+uneven-batch run over E/6V in [0.50, 0.75], across the transition; the
+network predicts the slopes at L = 20 and starts the Robbins-Monro iteration
+there with the gain offset n0.  Compared with the naive start a = -1, n0 = 0
+(Sec. 2.4 allows either): the predicted start is closer to the long
+reference run, it stays closer over the first steps, and the warm-started
+slopes still agree with the reference within 3 sigma.  Near the transition
+alone (E/6V around 0.6-0.66) the slopes are all close to -1, so there the
+naive start is itself within ~0.01-0.02 and the comparison says little; the
+wider range is where a start matters.
 """
 import numpy as np
 import pytest
@@ -25,11 +26,12 @@ def _built():
 
 
 def test_warm_start_beats_naive_start_at_L20():
-    data = warmstart.training_set(n_int=12, replicas=2, n_rm=30, n_therm=2, n_meas=6)
+    rng = dict(e_lo=0.50, e_hi=0.75)
+    data = warmstart.training_set(n_int=12, replicas=2, n_rm=30, n_therm=2, n_meas=6, **rng)
     assert np.all(np.isfinite(data["a"]))
     net, eps, loss = warmstart.fit_network(data, epochs=2000)
     assert eps < 0.05
-    target = workloads.warm_start_targets(20, replicas=4, n_int=8)
+    target = workloads.warm_start_targets(20, replicas=4, n_int=8, **rng)
     n_rm = 16
     res = warmstart.compare(target, net, eps, n_rm, 2, 6)
     net.close()
