@@ -59,6 +59,11 @@ def parse():
     p.add_argument("--phys-therm", type=int, default=5)
     p.add_argument("--phys-meas", type=int, default=20)
     p.add_argument("--phys-rm", type=int, default=0, help="0 = the paper's N_RM")
+    p.add_argument("--phys-intervals", default="512",
+                   help="intervals over the E range; a comma-separated list runs the "
+                        "discretisation study (C_V peak against dE^2, Sec. 3.5)")
+    p.add_argument("--phys-save", default="", help="write the final slopes a[replica][interval] "
+                                                    "to this .npy file")
     p.add_argument("--phases", action="store_true",
                    help="profiling driver: one overrelaxation pass, one heat-bath pass and one "
                         "composite sweep of 456 lattices of the workload (for ncu)")
@@ -426,14 +431,14 @@ PAPER_CV_PEAK = {8: (0.000551, 2e-6), 10: (0.000384, 2e-6), 12: (0.0002971, 1.1e
                  20: (0.0002007, 4e-7)}
 
 
-def physics_study(L, replicas, n_therm, n_meas, n_rm, beta_window=(1.0, 1.016)):
+def physics_study(L, replicas, n_therm, n_meas, n_rm, beta_window=(1.0, 1.016), n_int=512):
     """The whole LLR path at the paper's volume-study parameters: hot start,
     approach, n_rm graph-replayed Robbins-Monro iterations of every
     (interval, replica) chain from a = -1, then per replica ln rho and the
     specific-heat peak; returns the per-replica beta_c and var(E/6V) peak."""
     import torch
     from paper_1509_08391_gb300 import llr, workloads
-    w = workloads.paper_volume_study(L, replicas, n_therm, n_meas, n_rm)
+    w = workloads.paper_volume_study(L, replicas, n_therm, n_meas, n_rm, n_int=n_int)
     n = w.n_lattices
     stream = torch.cuda.Stream()
     t_all = time.perf_counter()
@@ -460,12 +465,21 @@ def physics_study(L, replicas, n_therm, n_meas, n_rm, beta_window=(1.0, 1.016)):
         b_r, v_r = llr.cv_peak(c, a[idx], beta_window[0], beta_window[1], n_grid=1601, tol=1e-10)
         bc.append(b_r)
         cv.append(v_r / six_v ** 2)
+    # the replica-mean slopes give one more estimate (averaging before the
+    # non-linear peak search)
+    a_rep = np.stack([a[np.where(rid == r)[0][np.argsort(iid[rid == r])]]
+                      for r in range(replicas)])
+    c_all = lo[np.where(rid == 0)[0][np.argsort(iid[rid == 0])]] + 0.5 * dE
+    b_m, v_m = llr.cv_peak(c_all, a_rep.mean(axis=0), beta_window[0], beta_window[1],
+                           n_grid=1601, tol=1e-10)
     upd = n * w.n_rm * (w.n_therm + w.n_meas) * (1 + w.n_or) * 4 * L ** 4
-    return {"workload": w.name, "L": L, "intervals": 512, "replicas": replicas, "dE": dE,
+    return {"workload": w.name, "L": L, "intervals": n_int, "replicas": replicas, "dE": dE,
             "E_over_6V": [lo.min() / six_v, (lo.max() + dE) / six_v],
             "n_therm": w.n_therm, "n_meas": w.n_meas, "n_rm": w.n_rm, "a0": w.a0,
             "status_ok": ok, "heat_bath_acceptance": float(st["hb_acc"].sum() / st["hb_tot"].sum()),
             "beta_c_per_replica": bc, "cv_peak_per_replica": cv,
+            "from_replica_mean_slopes": {"beta_c": b_m, "cv_peak": v_m / six_v ** 2},
+            "slopes": a_rep, "centres": c_all,
             "rm_seconds": t_rm, "wall_seconds": time.perf_counter() - t_all,
             "link_updates_per_s": upd / t_rm}
 
@@ -478,7 +492,15 @@ def run_physics(args):
     from paper_1509_08391_gb300 import build as bld
     bld.build()
     L = args.phys_L
-    res = physics_study(L, args.phys_replicas, args.phys_therm, args.phys_meas, args.phys_rm)
+    n_list = [int(x) for x in args.phys_intervals.split(",")]
+    if len(n_list) > 1:
+        run_discretisation(args, L, n_list)
+        return
+    res = physics_study(L, args.phys_replicas, args.phys_therm, args.phys_meas, args.phys_rm,
+                        n_int=n_list[0])
+    a_rep, centres = res.pop("slopes"), res.pop("centres")
+    if args.phys_save:
+        np.save(args.phys_save, np.vstack([centres[None, :], a_rep]))
     R = len(res["beta_c_per_replica"])
     for key, paper in (("beta_c", PAPER_BETA_C), ("cv_peak", PAPER_CV_PEAK)):
         v = np.asarray(res[key + "_per_replica"])
@@ -491,6 +513,39 @@ def run_physics(args):
             res[key]["deviation_sigma"] = (m - pv) / float(np.hypot(e, pe))
     res["metric"] = "beta_c(L) and C_V peak vs the paper (Tab. peakloc, Tab. peak)"
     print(json.dumps(res), flush=True)
+
+
+def run_discretisation(args, L, n_list):
+    """Sec. 3.5: the C_V peak against the interval width dE (the paper finds a
+    quadratic law, C_V(dE) = C_V(0) + b dE^2); one volume-study run per number
+    of intervals, then a weighted least-squares fit in dE^2."""
+    rows = []
+    for n_int in n_list:
+        res = physics_study(L, args.phys_replicas, args.phys_therm, args.phys_meas,
+                            args.phys_rm, n_int=n_int)
+        res.pop("slopes")
+        res.pop("centres")
+        v = np.asarray(res["cv_peak_per_replica"])
+        bc = np.asarray(res["beta_c_per_replica"])
+        R = v.size
+        rows.append({"intervals": n_int, "dE": res["dE"], "cv_peak": float(v.mean()),
+                     "cv_err": float(v.std(ddof=1) / np.sqrt(R)), "beta_c": float(bc.mean()),
+                     "beta_c_err": float(bc.std(ddof=1) / np.sqrt(R)),
+                     "rm_seconds": res["rm_seconds"], "status_ok": res["status_ok"]})
+    x = np.array([r["dE"] ** 2 for r in rows])
+    y = np.array([r["cv_peak"] for r in rows])
+    e = np.array([max(r["cv_err"], 1e-12) for r in rows])
+    A = np.stack([np.ones_like(x), x], axis=1) / e[:, None]
+    coef, *_ = np.linalg.lstsq(A, y / e, rcond=None)
+    cov = np.linalg.inv(A.T @ A)
+    chi2 = float(np.sum(((y - (coef[0] + coef[1] * x)) / e) ** 2))
+    out = {"metric": "C_V peak against dE (Sec. 3.5)", "L": L, "replicas": args.phys_replicas,
+           "n_therm": args.phys_therm, "n_meas": args.phys_meas, "rows": rows,
+           "fit": {"cv_peak_dE0": float(coef[0]), "cv_peak_dE0_err": float(np.sqrt(cov[0, 0])),
+                   "slope_per_dE2": float(coef[1]), "slope_err": float(np.sqrt(cov[1, 1])),
+                   "chi2": chi2, "dof": len(rows) - 2},
+           "paper_cv_peak_512": PAPER_CV_PEAK.get(L)}
+    print(json.dumps(out), flush=True)
 
 
 def run_phases(args):

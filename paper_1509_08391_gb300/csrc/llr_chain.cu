@@ -25,9 +25,10 @@
 //     Items run sweep-major, so uneven lattice sizes balance across SMs.
 //   * In a heat-bath pass the warps are specialised: producer warps build
 //     the six staples of one link per thread from 18 neighbour angles, draw
-//     the von Mises proposal (Best & Fisher 1979) and its dE, convert dE to
-//     int64 fixed point
-//     (2^-32) and form warp prefix sums; a consumer warp walks the chunks in
+//     the von Mises proposal (Best & Fisher 1979), evaluate its dE from the
+//     stored new angle exactly as the old local energy is evaluated, convert
+//     dE to int64 fixed point (2^-32) and form warp prefix sums; a consumer
+//     warp walks the chunks in
 //     link order and decides each block of B links with the restricted
 //     Metropolis rule dist(E + dE_block) <= dist(E), using a ballot to find
 //     the first rejected block among 32 speculatively accepted ones, then
@@ -35,8 +36,8 @@
 //     memory ring guarded by named barriers, so proposals for later chunks
 //     overlap with the scan of earlier ones.
 //   * Overrelaxation (theta' = -theta - 2 alpha) conserves E exactly, so its
-//     passes skip the scan: every warp reflects links and writes them
-//     directly.
+//     passes skip the scan: every thread reflects links (neighbours read with
+//     plain loads) and writes them directly.
 //   * The per-class update, energy and update functions are not inlined, so
 //     every program (batched sweeps, single passes, the plain form) runs the
 //     same machine code and gives bit-identical results.
@@ -62,11 +63,13 @@ constexpr int kStages = 4;
 // z = cos(pi u1), f = (1 + r z) / (r + z), c = k (r - f); accept if
 // c (2 - c) > u2 or ln(c / u2) + 1 - c >= 0.  The accept test runs on fast
 // hardware approximations (it only decides which attempt is taken); the
-// accepted variate is then evaluated accurately as (cos X, sin X), X = +-acos f:
-// with sh, ch = sin, cos(pi u1 / 2), z = ch^2 - sh^2 and
+// accepted variate is then evaluated without cancellation as (cos X, sin X),
+// X = +-acos f: with sh, ch = sin, cos(pi u1 / 2) (hardware sine/cosine,
+// absolute error ~5e-7 on [0, pi/2]), z = ch^2 - sh^2 and
 //   1 - f = (r - 1) 2 sh^2 / (r + z)   (f >= 0),   1 + f = (r + 1) 2 ch^2 / (r + z)   (f < 0),
 // so w = 1 -+ f has no cancellation, cos X = +-(1 - w) and
-// |sin X| = sqrt(w (2 - w)) keep full precision near X = 0 and X = pi.
+// |sin X| = sqrt(w (2 - w)) keep the angle's absolute accuracy near X = 0
+// and X = pi.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool von_mises(float kappa, uint32_t c0, uint32_t c1, uint32_t c2,
                                           uint32_t k0, uint32_t k1, float &cX, float &sX)
@@ -105,7 +108,7 @@ __device__ __forceinline__ bool von_mises(float kappa, uint32_t c0, uint32_t c1,
         }
     }
     if (!found) return false;
-    // ... then evaluate the accepted variate once, accurately
+    // ... then evaluate the accepted variate once, without cancellation
     const float u1 = u01(w_acc);
     float sh, ch;
     __sincosf(0.5f * kPi * u1, &sh, &ch);
@@ -339,7 +342,7 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, float *th, int p, floa
             float Sr, Si;
             staple_from<FAST>(stage_col<NT>(ch & 1), NT, Sr, Si);
             float so, co;
-            sincosf(t0, &so, &co);   // accurate: a biased cosine here biases every dE
+            sin_cos<FAST>(t0, &so, &co);
             const float e_old = co * Sr - so * Si;     // |S| cos(theta + alpha)
             const float Sabs = sqrtf(Sr * Sr + Si * Si);
             float cX, sX;
@@ -347,7 +350,17 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, float *th, int p, floa
             if (von_mises(-a_f * Sabs, link, sweep, tag, k0, k1, cX, sX)) {
                 // theta' = X - alpha, alpha = arg S: e^{i theta'} = e^{iX} conj(S) / |S|
                 thn = atan2f(sX * Sr - cX * Si, cX * Sr + sX * Si);
-                d = to_fx(Sabs * cX - e_old);            // theta' + alpha = X
+                // dE of the angle actually stored, evaluated exactly like e_old
+                // (same staple sum, same sine/cosine): the approximation errors
+                // of one link's successive evaluations then cancel along its
+                // chain of updates and leave only random noise.  Taking
+                // |S| cos X instead carried a systematic -3.5e-8 per move (the
+                // rounded atan2 and (cos X, sin X) are not exactly the angle
+                // X - alpha), which drifted the running energy by -4.8e-4 per
+                // heat-bath pass at L = 8 and shifted the window it enforces.
+                float sn, cn;
+                sin_cos<FAST>(thn, &sn, &cn);
+                d = to_fx((cn * Sr - sn * Si) - e_old);
             } else {
                 thn = t0;
                 atomicAdd(&sm.cap_cnt, 1ull);

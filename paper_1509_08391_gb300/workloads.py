@@ -163,15 +163,15 @@ PAPER_VOLUME_STUDY = {
 
 
 def paper_volume_study(L: int, replicas: int = 8, n_therm: int = 5, n_meas: int = 20,
-                       n_rm: int = 0) -> Workload:
-    """The paper's L^4 study (Tab. SimDet): 512 contiguous intervals of width
-    dE = (E_max - E_min) / 512 over its E/6V range, `replicas` independent
-    chains per interval (the paper repeats each run N_B = 20 times), N_RM
-    Robbins-Monro iterations (the paper's value when n_rm = 0).  Sweeps per
-    iteration are composite sweeps (1 heat-bath + 4 overrelaxation passes)."""
+                       n_rm: int = 0, n_int: int = 512) -> Workload:
+    """The paper's L^4 study (Tab. SimDet): n_int (512) contiguous intervals of
+    width dE = (E_max - E_min) / n_int over its E/6V range (other n_int: the
+    discretisation study, Tab. descaling), `replicas` independent chains per
+    interval (the paper repeats each run N_B = 20 times), N_RM Robbins-Monro
+    iterations (the paper's value when n_rm = 0).  Sweeps per iteration are
+    composite sweeps (1 heat-bath + 4 overrelaxation passes)."""
     e_lo, e_hi, _n_sw, n_rm_paper = PAPER_VOLUME_STUDY[L]
-    n_int = 512
     dE = 6.0 * L ** 4 * (e_hi - e_lo) / n_int
-    return _grid("u1_4d_L%d_512int_x%d_paper" % (L, replicas), [L], n_int, e_lo, e_hi, [dE],
+    return _grid("u1_4d_L%d_%dint_x%d_paper" % (L, n_int, replicas), [L], n_int, e_lo, e_hi, [dE],
                  replicas, SEED_BASE + 10 + L, n_therm=n_therm, n_meas=n_meas,
                  n_rm=n_rm if n_rm > 0 else n_rm_paper)
