@@ -262,3 +262,30 @@ def test_approach_reaches_window_and_stays(side):
     for _ in range(10):
         t.sweep(-1.0, 1)
         assert E_lo <= t.E <= E_lo + 4.0
+
+
+def test_robbins_monro_step_matches_eq_kk21_on_the_exact_mean():
+    """One Robbins-Monro step from a = root + 0.5 on the 2-plaquette strip, the
+    chain equilibrated at that a first: averaged over replicas, the step equals
+    12 (<<E>>(a) - E_lo - dE/2) / (dE^2 (n + 1)) with <<E>>(a) from the
+    quadrature of eq. kk9, for n = 0 and n = 3.  A wrong gain constant, sign
+    or step offset moves the mean step by a factor of 2 or more."""
+    lo, hi = 0.5, 1.1
+    dE = hi - lo
+    root = exact2d.llr_root_2plaq(lo, hi)
+    a0 = root + 0.5
+    exact_mean = exact2d.restricted_mean_2plaq(lo, hi, a0)
+    g = oracle.Geom([3, 2], periodic=False)
+    for n in (0, 3):
+        want = 12.0 * (exact_mean - lo - 0.5 * dE) / (dE * dE * (n + 1))
+        steps = []
+        for r in range(64):
+            t = oracle.Lattice(g, 2024, 3, r, lo, dE, n_or=1, block=1)
+            t.hot_start()
+            assert t.approach(10000) >= 0
+            a1, _ = t.rm_step(a0, 200, 1600, n)
+            steps.append(a1 - a0)
+        steps = np.array(steps)
+        err = steps.std(ddof=1) / np.sqrt(steps.size)
+        assert abs(steps.mean() - want) < 4 * err + 0.02 * abs(want), (n, steps.mean(), want, err)
+        assert 4 * err < 0.25 * abs(want)        # resolves a factor-2 error in the gain
