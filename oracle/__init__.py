@@ -85,6 +85,11 @@ def lib():
                                       D, D, I, ip, dp]),
                 "orc_batch_sweeps": (None, [P, dp, I, I, I]),
                 "orc_replica_exchange": (I, [P, I, ip, dp, U32, ip]),
+                "orc_muca_new": (P, [I, D, D, dp]),
+                "orc_muca_free": (None, [P]),
+                "orc_muca_lnrho": (D, [P, D]),
+                "orc_lat_muca_sweep": (None, [P, P, D, I, dp]),
+                "orc_lat_muca_class_trace": (I, [P, P, I, D, dp, dp, dp, dp, ip]),
                 "orc_batch_approach": (None, [P, ip, I, I, I]),
             }
             for name, (res, args) in sig.items():
@@ -255,6 +260,48 @@ class Lattice:
         a_new = lib().orc_lat_rm_step(self._h, float(a), int(n_therm), int(n_meas),
                                       int(rm_index), ctypes.byref(m))
         return a_new, m.value
+
+
+class MucaWeight:
+    """ln rho~ of eq. rhoguess from the slopes of n contiguous intervals of width
+    de starting at e0, continued linearly beyond them: the weight 1/rho~ of the
+    multicanonical run (Sec. 2.6, eq. 4.1)."""
+
+    def __init__(self, e0, de, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        self._a = a
+        self._h = lib().orc_muca_new(len(a), float(e0), float(de), _dp(a))
+        if not self._h:
+            raise ValueError("bad multicanonical table")
+
+    def lnrho(self, E):
+        return lib().orc_muca_lnrho(self._h, float(E))
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().orc_muca_free(self._h)
+        except Exception:
+            pass
+
+
+def muca_sweep(lattice, weight, a0, n_sweeps):
+    """n multicanonical composite sweeps; returns the energy after each."""
+    out = np.zeros(int(n_sweeps))
+    lib().orc_lat_muca_sweep(lattice._h, weight._h, float(a0), int(n_sweeps), _dp(out))
+    return out
+
+
+def muca_class_trace(lattice, weight, cls, a0):
+    """One multicanonical heat-bath class: per link (update order) the energy
+    before it, its dE, the uniform u, the exponent x and the decision."""
+    n = lattice.geom.nslot
+    bufs = [np.zeros(n) for _ in range(4)]
+    acc = np.zeros(n, dtype=np.int32)
+    m = lib().orc_lat_muca_class_trace(lattice._h, weight._h, int(cls), float(a0), _dp(bufs[0]),
+                                       _dp(bufs[1]), _dp(bufs[2]), _dp(bufs[3]), _ip(acc))
+    return dict(E_before=bufs[0][:m], dE=bufs[1][:m], u=bufs[2][:m], x=bufs[3][:m],
+                accepted=acc[:m].astype(bool))
 
 
 def batch_run(geom: Geom, seed, interval_id, replica_id, E_lo, dE, a0, n_or=4, block=1,

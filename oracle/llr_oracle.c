@@ -61,6 +61,16 @@
  *      intervals tried in one exchange round and a round number; the draw
  *      deciding a pair comes from Philox keyed by the pair's first lattice,
  *      counter (0, round, swap tag, 0), as a 53-bit uniform in [0, 1).
+ *   R8 multicanonical run (Sec. 2.6, eq. 4.1): weight W(E) = 1/rho~(E), with
+ *      ln rho~ the piecewise-linear function of eq. rhoguess built from the
+ *      slopes of n contiguous intervals and continued linearly with the end
+ *      slopes outside them (the micro-canonical beta_1, beta_2 tails).  A
+ *      heat-bath pass proposes every link of a class from its conditional
+ *      at a fixed slope a0 (the same proposals as the restricted heat-bath)
+ *      and accepts them in link order by Metropolis-Hastings for W:
+ *      u < exp(a0 dE - (ln rho~(E + dE) - ln rho~(E))), u from Philox
+ *      counter (link, sweep, 12, 0) word 0.  Overrelaxation passes keep E
+ *      and are always taken.
  */
 #include <math.h>
 #include <stdint.h>
@@ -259,6 +269,7 @@ typedef struct {
 } orc_lat;
 
 #define TAG_HB 0u
+#define TAG_MUCA 12u
 #define TAG_SWAP 13u
 #define TAG_APPROACH 14u
 #define TAG_INIT 15u
@@ -634,6 +645,117 @@ int orc_replica_exchange(orc_lat **lats, int n_pairs, const int *pairs, const do
         n_acc += acc;
     }
     return n_acc;
+}
+
+/* ------------------------------------------------------------------------
+ * Multicanonical update (Sec. 2.6, eq. 4.1).  ln rho~ at the edges of n
+ * contiguous intervals of width de from e0: lnr[0] = 0,
+ * lnr[k+1] = lnr[k] + a_k de (eq. rhoguess), linear with slope a_k inside
+ * interval k and with the first / last slope beyond the ends.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int n;
+    double e0, de;
+    double *lnr, *a;
+} orc_muca;
+
+orc_muca *orc_muca_new(int n, double e0, double de, const double *a)
+{
+    if (n < 1 || !(de > 0.0)) return NULL;
+    orc_muca *m = (orc_muca *)calloc(1, sizeof(orc_muca));
+    m->n = n; m->e0 = e0; m->de = de;
+    m->lnr = (double *)calloc((size_t)n + 1, sizeof(double));
+    m->a = (double *)calloc((size_t)n, sizeof(double));
+    for (int k = 0; k < n; ++k) {
+        m->a[k] = a[k];
+        m->lnr[k + 1] = m->lnr[k] + a[k] * de;
+    }
+    return m;
+}
+
+void orc_muca_free(orc_muca *m)
+{
+    if (!m) return;
+    free(m->lnr); free(m->a); free(m);
+}
+
+double orc_muca_lnrho(const orc_muca *m, double E)
+{
+    int k = (int)floor((E - m->e0) / m->de);
+    if (k < 0) k = 0;
+    if (k > m->n - 1) k = m->n - 1;
+    return m->lnr[k] + m->a[k] * (E - (m->e0 + k * m->de));
+}
+
+/* One class of a multicanonical heat-bath pass: proposals as in
+ * group_update (heat-bath at slope a0, tag TAG_HB), then Metropolis-Hastings
+ * for the weight 1/rho~ in link order.  Optional trace per link (update
+ * order): energy before, dE, u, exponent, accepted. */
+static void muca_class(orc_lat *t, const orc_muca *m, int cls, double a0, double *tr_E,
+                       double *tr_dE, double *tr_u, double *tr_x, int *tr_acc)
+{
+    const orc_geom *g = t->g;
+    int c0 = g->class_start[cls], c1 = g->class_start[cls + 1];
+    double phi[8];
+    for (int i = c0; i < c1; ++i) {
+        int l = g->class_links[i];
+        int n = staples(t, l, phi);
+        double Sr = 0.0, Si = 0.0;
+        for (int j = 0; j < n; ++j) { Sr += cos(phi[j]); Si += sin(phi[j]); }
+        double alpha = atan2(Si, Sr), Sabs = sqrt(Sr * Sr + Si * Si);
+        double th = t->theta[l], thn, X;
+        int att = orc_vonmises(-a0 * Sabs, t->key, (uint32_t)l, t->sweep, TAG_HB, &X);
+        if (att < 0) { thn = th; t->caps += 1.0; }
+        else thn = wrap_angle(X - alpha);
+        t->prop[l] = thn;
+        t->dEl[l] = local_energy(n, phi, thn) - local_energy(n, phi, th);
+    }
+    for (int i = c0; i < c1; ++i) {
+        int l = g->class_links[i];
+        double d = t->dEl[l];
+        double x = a0 * d - (orc_muca_lnrho(m, t->E + d) - orc_muca_lnrho(m, t->E));
+        uint32_t ctr[4] = {(uint32_t)l, t->sweep, TAG_MUCA, 0u}, w[4];
+        orc_philox4x32_10(ctr, t->key, w);
+        double u = orc_uniform(w[0]);
+        int acc = u < exp(x);
+        if (tr_E) {
+            tr_E[i - c0] = t->E; tr_dE[i - c0] = d; tr_u[i - c0] = u; tr_x[i - c0] = x;
+            tr_acc[i - c0] = acc;
+        }
+        if (acc) { t->theta[l] = t->prop[l]; t->E += d; t->hb_acc += 1.0; }
+        t->hb_tot += 1.0;
+    }
+}
+
+/* n composite multicanonical sweeps: heat-bath pass (classes in order),
+ * n_or overrelaxation passes (always taken), fresh-energy resync.  E_out
+ * (nullable) receives the energy after each sweep. */
+void orc_lat_muca_sweep(orc_lat *t, const orc_muca *m, double a0, int n_sweeps, double *E_out)
+{
+    const orc_geom *g = t->g;
+    double lo = t->E_lo, w = t->dE;
+    for (int s = 0; s < n_sweeps; ++s) {
+        for (int cls = 0; cls < 2 * g->d; ++cls) muca_class(t, m, cls, a0, 0, 0, 0, 0, 0);
+        t->E_lo = -1e300; t->dE = 2e300;   /* overrelaxation keeps E: no window */
+        for (int k = 0; k < t->n_or; ++k) pass(t, 1, 0.0, TAG_HB);
+        t->E_lo = lo; t->dE = w;
+        double fresh = orc_energy(t);
+        double drift = fabs(fresh - t->E);
+        if (drift > t->max_drift) t->max_drift = drift;
+        t->E = fresh;
+        t->sweep += 1u;
+        if (E_out) E_out[s] = t->E;
+    }
+}
+
+/* One multicanonical heat-bath class with its per-link trace (tests);
+ * returns the number of links of the class. */
+int orc_lat_muca_class_trace(orc_lat *t, const orc_muca *m, int cls, double a0, double *E_before,
+                             double *dE, double *u, double *x, int *accepted)
+{
+    if (cls < 0 || cls >= 2 * t->g->d) return 0;
+    muca_class(t, m, cls, a0, E_before, dE, u, x, accepted);
+    return t->g->class_start[cls + 1] - t->g->class_start[cls];
 }
 
 /* Per-link staple modulus |S| and angle alpha (for invariance checks). */

@@ -97,3 +97,16 @@ def restricted_moments_3plaq(lo: float, hi: float, a: float, kmax: int = 1, n_ou
 def restricted_mean_3plaq(lo, hi, a):
     m = restricted_moments_3plaq(lo, hi, a, 1)
     return m[1] / m[0]
+
+
+def density_2plaq(E: float) -> float:
+    """Density of E = cos p1 + cos p2 for independent uniform plaquette angles
+    (normalised: its integral over E is 1): the convolution of two
+    arcsine densities 1 / (pi sqrt(1 - e^2)), evaluated with the endpoint
+    singularities as an algebraic quadrature weight.  0 < |E| < 2."""
+    E = abs(E)
+    lo, hi = E - 1.0, 1.0
+    f = lambda e: 1.0 / np.sqrt((1.0 + e) * (1.0 + E - e))
+    val = integrate.quad(f, lo, hi, weight="alg", wvar=(-0.5, -0.5), epsabs=1e-13,
+                         epsrel=1e-12, limit=200)[0]
+    return float(val / np.pi ** 2)
