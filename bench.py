@@ -64,6 +64,12 @@ def parse():
                         "discretisation study (C_V peak against dE^2, Sec. 3.5)")
     p.add_argument("--phys-save", default="", help="write the final slopes a[replica][interval] "
                                                     "to this .npy file")
+    p.add_argument("--muca", action="store_true",
+                   help="multicanonical check of Sec. 2.6 at L = 8: LLR slopes of a coarse volume "
+                        "study, then chains with the weight 1/rho~: histogram flatness, round "
+                        "trips, reweighted <E> and C_V peak against the LLR reconstruction")
+    p.add_argument("--muca-chains", type=int, default=512)
+    p.add_argument("--muca-sweeps", type=int, default=4000)
     p.add_argument("--phases", action="store_true",
                    help="profiling driver: one overrelaxation pass, one heat-bath pass and one "
                         "composite sweep of 456 lattices of the workload (for ncu)")
@@ -548,6 +554,118 @@ def run_discretisation(args, L, n_list):
     print(json.dumps(out), flush=True)
 
 
+def lnrho_table(e0, de, a, E):
+    """ln rho~ of eq. rhoguess at energies E (numpy, for the analysis of the
+    multicanonical samples): 0 at e0, slope a[k] in interval k, the end slopes
+    beyond the table."""
+    lnr = np.concatenate([[0.0], np.cumsum(np.asarray(a) * de)])
+    k = np.clip(np.floor((E - e0) / de).astype(np.int64), 0, len(a) - 1)
+    return lnr[k] + np.asarray(a)[k] * (E - (e0 + k * de))
+
+
+def run_muca(args):
+    """--muca: the ergodicity check of Sec. 2.6 at L = 8.  (1) LLR slopes of
+    the paper's L = 8 range in 64 intervals (4 replicas, 300 Robbins-Monro
+    steps); (2) independent multicanonical chains with W = 1/rho~ from the
+    replica-mean slopes; (3) the energy histogram over the range, the round
+    trips between its ends, and <E>, C_V(beta) reweighted from the
+    multicanonical samples with W^-1 (eq. 4.7) against the LLR reconstruction
+    of the same slopes (eqs. l19/l20)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1509_08391_gb300 import build as bld
+    bld.build()
+    from paper_1509_08391_gb300 import llr, workloads
+    L, n_int = 8, 64
+    six_v = 6.0 * L ** 4
+    t_all = time.perf_counter()
+    w = workloads.paper_volume_study(L, replicas=4, n_therm=5, n_meas=20, n_rm=300, n_int=n_int)
+    stream = torch.cuda.Stream()
+    with llr.Batch.from_workload(w, stream=stream.cuda_stream, max_approach=5000) as b:
+        a_dev = torch.full((w.n_lattices,), w.a0, dtype=torch.float64, device="cuda")
+        b.rm_run(a_dev, w.n_therm, w.n_meas, 0, w.n_rm)
+        torch.cuda.synchronize()
+        a = a_dev.cpu().numpy()
+    iid = np.asarray(w.interval_id)
+    uniq = np.unique(iid)
+    a_k = np.array([a[iid == k].mean() for k in uniq])
+    lo = np.array([w.E_lo[np.nonzero(iid == k)[0][0]] for k in uniq])
+    dE = w.dE[0]
+    e_min, e_max = lo[0], lo[-1] + dE
+    centres = lo + 0.5 * dE
+    # multicanonical chains: hot start, approach into [E_min, E_max], then W = 1/rho~
+    nc = args.muca_chains
+    wm = workloads.Workload("u1_4d_L8_muca_x%d" % nc, [L] * nc, [e_min] * nc, [e_max - e_min] * nc,
+                            list(range(nc)), [0] * nc, workloads.SEED_BASE + 40)
+    a0 = float(a_k.mean())
+    t0 = time.perf_counter()
+    with llr.Batch.from_workload(wm, stream=stream.cuda_stream, max_approach=5000) as b:
+        b.set_muca_weight(e_min, dE, a_k, a0)
+        b.muca_sweep(200, history=False)
+        E = b.muca_sweep(args.muca_sweeps)
+        st = b.stats()
+    t_muca = time.perf_counter() - t0
+    # (3) flatness over the table's range
+    h, _ = np.histogram(E.ravel(), bins=np.linspace(e_min, e_max, 17))
+    frac = h / h.mean()
+    # round trips between the lowest and the highest tenth of the range
+    span = e_max - e_min
+    trips = 0
+    for c in range(nc):
+        state = 0
+        for e in E[:, c]:
+            if e < e_min + 0.1 * span and state != -1:
+                trips += state == 1
+                state = -1
+            elif e > e_max - 0.1 * span and state != 1:
+                trips += state == -1
+                state = 1
+    # reweighting (eq. 4.7): a sample at E carries e^{beta E} / W(E) = e^{beta E + ln rho~(E)}
+    x = E.ravel()
+    lr = lnrho_table(e_min, dE, a_k, x)
+    betas = np.linspace(1.000, 1.016, 1601)
+
+    def moments(beta, xs, lrs):
+        lw = beta * xs + lrs
+        wgt = np.exp(lw - lw.max())
+        m1 = np.sum(wgt * xs) / wgt.sum()
+        m2 = np.sum(wgt * xs * xs) / wgt.sum()
+        return m1, m2 - m1 * m1
+
+    def peak(xs, lrs):
+        cv = np.array([moments(bb, xs, lrs)[1] for bb in betas[::8]])
+        i = int(np.argmax(cv))
+        fine = betas[max(0, 8 * i - 8):8 * i + 9]
+        cvf = np.array([moments(bb, xs, lrs)[1] for bb in fine])
+        j = int(np.argmax(cvf))
+        return float(fine[j]), float(cvf[j] / six_v ** 2)
+
+    b_mu, cv_mu = peak(x, lr)
+    # spread of the reweighted peak over independent groups of chains
+    groups = np.array_split(np.arange(nc), 8)
+    grp = [peak(E[:, gidx].ravel(), lnrho_table(e_min, dE, a_k, E[:, gidx].ravel()))
+           for gidx in groups]
+    gb = np.array([g[0] for g in grp])
+    gc = np.array([g[1] for g in grp])
+    b_llr, cv_llr = llr.cv_peak(centres, a_k, 1.0, 1.016, n_grid=1601, tol=1e-10)
+    E_mu_c = moments(b_llr, x, lr)[0] / six_v
+    _, E1, _ = llr.observables(centres, a_k, [b_llr])
+    out = {"metric": "multicanonical reweighting vs LLR reconstruction (Sec. 2.6)", "L": L,
+           "llr": {"intervals": n_int, "replicas": 4, "n_rm": w.n_rm, "dE": dE,
+                   "beta_c": b_llr, "cv_peak": cv_llr / six_v ** 2},
+           "muca": {"chains": nc, "sweeps": args.muca_sweeps, "a0": a0,
+                    "heat_bath_acceptance": float(st["hb_acc"].sum() / st["hb_tot"].sum()),
+                    "histogram_over_range": [float(f) for f in frac],
+                    "histogram_max_dev": float(np.max(np.abs(frac - 1.0))),
+                    "round_trips": int(trips), "seconds": t_muca,
+                    "beta_c": b_mu, "beta_c_err": float(gb.std(ddof=1) / np.sqrt(len(gb))),
+                    "cv_peak": cv_mu, "cv_peak_err": float(gc.std(ddof=1) / np.sqrt(len(gc)))},
+           "E_over_6V_at_llr_beta_c": {"muca": E_mu_c, "llr": float(E1[0] / six_v)},
+           "paper": {"beta_c": PAPER_BETA_C[L], "cv_peak": PAPER_CV_PEAK[L]},
+           "wall_seconds": time.perf_counter() - t_all}
+    print(json.dumps(out), flush=True)
+
+
 def run_phases(args):
     """One launch per pass kind on 456 lattices of the benchmark workload (one
     full wave of 256-thread CTAs: 3 per SM on 152 SMs), so an ncu capture
@@ -579,6 +697,9 @@ def main():
         return
     if args.physics:
         run_physics(args)
+        return
+    if args.muca:
+        run_muca(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -90,7 +90,8 @@ int llr_sweep(llr_handle h, const double *a, int n_sweeps, int measure, double *
 /* One pass of a composite sweep for every lattice, without the energy
  * resync and without advancing the sweep counter: kind 0 = heat-bath at the
  * slopes a (host double[n_lattices]), kind 1 = overrelaxation (a may be
- * NULL).  Each selected checkerboard class (bit c of class_mask selects
+ * NULL), kind 2 = the multicanonical heat-bath pass of llr_muca_sweep (a is
+ * ignored; needs llr_set_muca_weight).  Each selected checkerboard class (bit c of class_mask selects
  * class c = 2 mu + parity; 0xFF = the whole pass, in class order) draws its
  * proposals and accepts them in link order with the window rule of
  * llr_sweep.  Synchronous. */
@@ -129,6 +130,28 @@ int llr_rm_run(llr_handle h, int n_therm, int n_meas, int rm_index0, int n_steps
  * no graph).  Same arguments and results as llr_rm_step.  Synchronous. */
 int llr_rm_step_plain(llr_handle h, int n_therm, int n_meas, int rm_index, double *a_inout,
                       double *dE_mean_out);
+
+/* Weight of the multicanonical run (Sec. 2.6, eq. 4.1): W(E) = 1/rho~(E),
+ * with ln rho~ the piecewise-linear density of eq. rhoguess on n contiguous
+ * intervals of width de starting at e0 (ln rho~ = 0 at e0, slope a[k] inside
+ * interval k) and continued beyond the first / last interval with their
+ * slopes (the tails of eq. 4.1 at the micro-canonical beta_1, beta_2).
+ * a0 is the slope of the heat-bath proposals (any value; Metropolis-Hastings
+ * corrects it, and a0 near the slopes keeps the acceptance high).  a: host
+ * double[n].  Copied to the device; applies to every lattice of the handle.
+ * Errors: LLR_ERR_ARG for n < 1, de <= 0 or a non-finite value. */
+int llr_set_muca_weight(llr_handle h, int n, double e0, double de, const double *a, double a0);
+
+/* n_sweeps multicanonical composite sweeps of every lattice (Sec. 2.6):
+ * a heat-bath pass whose proposals (the conditional at slope a0, the same
+ * draws as the restricted heat-bath) are taken in link order with
+ * probability min(1, exp(a0 dE - (ln rho~(E + dE) - ln rho~(E)))) (uniform
+ * from Philox counter (link, sweep, 12, 0)), n_or overrelaxation passes
+ * (they keep E, so any weight of E accepts them), and the fresh-energy
+ * resync.  No window is imposed.  E_out: host double[n_sweeps][n_lattices],
+ * the energy after each sweep, or NULL.  Synchronous.
+ * Errors: LLR_ERR_ARG if no weight was set. */
+int llr_muca_sweep(llr_handle h, int n_sweeps, double *E_out);
 
 /* One round of replica exchange between overlapping intervals (Sec. 2.5).
  * For each pair (I1, I2) = (pairs[2k], pairs[2k+1]) of lattice indices: if

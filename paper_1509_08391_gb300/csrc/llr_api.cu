@@ -37,6 +37,12 @@ struct llr_ctx {
     int *d_order = nullptr;          // 0 .. n-1 (single-lattice launches point into it)
     int *d_step = nullptr;           // Robbins-Monro step counter of graph replays
     int *d_pairs = nullptr;          // replica-exchange pairs (n ints: at most n/2 pairs)
+    // multicanonical weight: ln rho~ at the n + 1 edges, then the n slopes
+    double *d_muca = nullptr;
+    int muca_n = 0;
+    double muca_e0 = 0.0, muca_de = 0.0, muca_a0 = 0.0;
+    double *d_ehist = nullptr;       // energy history of llr_muca_sweep
+    size_t ehist_cap = 0;
     // one captured Robbins-Monro step (memset, persistent kernel, step + 1)
     cudaGraphExec_t rm_graph = nullptr;
     int g_therm = -1, g_meas = -1, g_index0 = -1;
@@ -266,13 +272,23 @@ int llr_sweep(llr_handle h, const double *a_host, int n_sweeps, int measure, dou
 int llr_pass(llr_handle h, int kind, const double *a_host, int class_mask)
 {
     if (int r = check_handle(h)) return r;
-    if (kind != 0 && kind != 1) return fail(LLR_ERR_ARG, "kind must be 0 (heat-bath) or 1");
+    if (kind < 0 || kind > 2)
+        return fail(LLR_ERR_ARG, "kind must be 0 (heat-bath), 1 (overrelaxation) or 2 (multicanonical)");
     if (class_mask < 1 || class_mask > 0xFF) return fail(LLR_ERR_ARG, "class_mask must be in 1..255");
     if (kind == 0 && !a_host) return fail(LLR_ERR_ARG, "heat-bath pass needs a");
+    if (kind == 2 && !h->d_muca) return fail(LLR_ERR_ARG, "no multicanonical weight set");
     llr::KernelArgs a = base_args(h);
     a.program = llr::kProgPass;
     a.pass_kind = kind;
     a.class_mask = class_mask;
+    if (kind == 2) {
+        a.muca_lnr = h->d_muca;
+        a.muca_a = h->d_muca + h->muca_n + 1;
+        a.muca_n = h->muca_n;
+        a.muca_e0 = h->muca_e0;
+        a.muca_de = h->muca_de;
+        a.muca_a0 = h->muca_a0;
+    }
     if (a_host) {
         LLR_CUDA(cudaMemcpyAsync(h->d_a, a_host, sizeof(double) * (size_t)h->n,
                                  cudaMemcpyHostToDevice, h->stream));
@@ -446,6 +462,70 @@ int llr_replica_exchange(llr_handle h, int n_pairs, const int *pairs, const doub
                                  cudaMemcpyDeviceToHost, h->stream));
     LLR_CUDA(cudaStreamSynchronize(h->stream));
     return LLR_OK;
+}
+
+int llr_set_muca_weight(llr_handle h, int n, double e0, double de, const double *a_host,
+                        double a0)
+{
+    if (int r = check_handle(h)) return r;
+    if (n < 1 || !a_host || !std::isfinite(e0) || !std::isfinite(de) || !(de > 0.0) ||
+        !std::isfinite(a0))
+        return fail(LLR_ERR_ARG, "need n >= 1 finite slopes, finite e0, de > 0 and finite a0");
+    std::vector<double> tab(2 * (size_t)n + 1);
+    tab[0] = 0.0;
+    for (int k = 0; k < n; ++k) {
+        if (!std::isfinite(a_host[k])) return fail(LLR_ERR_ARG, "non-finite slope");
+        tab[(size_t)k + 1] = tab[(size_t)k] + a_host[k] * de;   // eq. rhoguess at the edges
+        tab[(size_t)n + 1 + (size_t)k] = a_host[k];
+    }
+    if (h->d_muca && h->muca_n != n) {
+        LLR_CUDA(cudaStreamSynchronize(h->stream));
+        cudaFree(h->d_muca);
+        h->d_muca = nullptr;
+    }
+    if (!h->d_muca) LLR_CUDA(cudaMalloc(&h->d_muca, sizeof(double) * tab.size()));
+    LLR_CUDA(cudaMemcpyAsync(h->d_muca, tab.data(), sizeof(double) * tab.size(),
+                             cudaMemcpyHostToDevice, h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    h->muca_n = n;
+    h->muca_e0 = e0;
+    h->muca_de = de;
+    h->muca_a0 = a0;
+    return LLR_OK;
+}
+
+int llr_muca_sweep(llr_handle h, int n_sweeps, double *E_out)
+{
+    if (int r = check_handle(h)) return r;
+    if (n_sweeps < 0) return fail(LLR_ERR_ARG, "n_sweeps must be >= 0");
+    if (!h->d_muca) return fail(LLR_ERR_ARG, "no multicanonical weight set");
+    if (n_sweeps == 0) return LLR_OK;
+    const size_t need = (size_t)n_sweeps * (size_t)h->n;
+    if (E_out && h->ehist_cap < need) {
+        LLR_CUDA(cudaStreamSynchronize(h->stream));
+        cudaFree(h->d_ehist);
+        h->d_ehist = nullptr;
+        h->ehist_cap = 0;
+        LLR_CUDA(cudaMalloc(&h->d_ehist, sizeof(double) * need));
+        h->ehist_cap = need;
+    }
+    llr::KernelArgs a = base_args(h);
+    a.program = llr::kProgMuca;
+    a.n_therm = 0;
+    a.n_meas = n_sweeps;
+    a.muca_lnr = h->d_muca;
+    a.muca_a = h->d_muca + h->muca_n + 1;
+    a.muca_n = h->muca_n;
+    a.muca_e0 = h->muca_e0;
+    a.muca_de = h->muca_de;
+    a.muca_a0 = h->muca_a0;
+    a.e_hist = E_out ? h->d_ehist : nullptr;
+    LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
+    if (E_out)
+        LLR_CUDA(cudaMemcpyAsync(E_out, h->d_ehist, sizeof(double) * need, cudaMemcpyDeviceToHost,
+                                 h->stream));
+    LLR_CUDA(cudaStreamSynchronize(h->stream));
+    return check_queue(h);
 }
 
 int llr_energy(llr_handle h, double *E_out)
@@ -639,6 +719,8 @@ int llr_destroy(llr_handle h)
     cudaFree(h->d_order);
     cudaFree(h->d_step);
     cudaFree(h->d_pairs);
+    cudaFree(h->d_muca);
+    cudaFree(h->d_ehist);
     if (h->rm_graph) cudaGraphExecDestroy(h->rm_graph);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     delete h;

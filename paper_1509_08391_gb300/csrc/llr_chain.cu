@@ -547,13 +547,89 @@ __device__ __noinline__ void consume_class(Smem<NWP> &sm, int B, int nchunk)
     if (lane == 0) sm.st.E_fx = E;
 }
 
+// ln rho~ of the multicanonical weight at the fixed-point energy E: the
+// piecewise-linear function of eq. rhoguess on the table's intervals,
+// continued with the first / last slope beyond them (Sec. 2.6, eq. 4.1).
+__device__ __forceinline__ double muca_lnrho(const KernelArgs &a, long long E_fx)
+{
+    const double E = (double)E_fx * kInvFx;
+    int k = (int)floor((E - a.muca_e0) / a.muca_de);
+    k = k < 0 ? 0 : (k > a.muca_n - 1 ? a.muca_n - 1 : k);
+    return a.muca_lnr[k] + a.muca_a[k] * (E - (a.muca_e0 + (double)k * a.muca_de));
+}
+
+// Consumer side of a multicanonical heat-bath class (Sec. 2.6): the links
+// of each 32-link group are taken in link order by Metropolis-Hastings for
+// the weight 1/rho~ with the proposal at slope a0, i.e. with probability
+// min(1, exp(a0 dE - (ln rho~(E + dE) - ln rho~(E)))), E the running energy
+// before the link; the uniform comes from Philox counter (link, sweep, 12, 0).
+// Speculatively every remaining link is decided as if all earlier ones were
+// taken; the first refusal (one ballot) fixes the links before it, its dE is
+// dropped and the rest is decided again.  Blocks of one link.
+template <int NWP>
+__device__ __noinline__ void consume_class_muca(Smem<NWP> &sm, int nchunk, int mu, int p,
+                                                const KernelArgs &args)
+{
+    constexpr int NT = (NWP + 1) * 32, CH = NWP * 32;
+    const int lane = threadIdx.x & 31;
+    const int L = sm.st.L, half = sm.st.half;
+    const uint32_t magic = sm.st.magic, V = 2u * (uint32_t)half;
+    const uint32_t k0 = sm.st.key0, k1 = sm.st.key1, sweep = sm.st.sweep;
+    const double a0 = args.muca_a0;
+    long long E = sm.st.E_fx;
+    for (int ch = 0; ch < nchunk; ++ch) {
+        const int s = ch & (kStages - 1);
+        bar_sync(1 + s, NT);
+        Stage<NWP> &stg = sm.stage[s];
+        for (int g = 0; g < NWP; ++g) {
+            const unsigned em = stg.endmask[g];
+            unsigned rem = em, acc = 0u;
+            const long long Pk = stg.P[g * 32 + lane];
+            const long long Pprev = __shfl_up_sync(kFull, Pk, 1);
+            const long long dk = lane > 0 ? Pk - Pprev : Pk;
+            double u = 1.0;
+            if ((em >> lane) & 1u) {
+                int x[4];
+                const int site = decode_half(ch * CH + g * 32 + lane, p, L, magic, x);
+                const U4 w = philox4x32_10((uint32_t)mu * V + (uint32_t)site, sweep, kTagMuca, 0u,
+                                           k0, k1);
+                u = (double)u01(w.x);
+            }
+            long long R = 0;
+            while (rem) {
+                const bool mine = (rem >> lane) & 1u;
+                bool refuse = false;
+                if (mine) {
+                    const long long Eb = E + (Pk - dk) - R;
+                    const double xk =
+                        a0 * ((double)dk * kInvFx) - (muca_lnrho(args, Eb + dk) - muca_lnrho(args, Eb));
+                    refuse = !(u < exp(xk));
+                }
+                const unsigned vm = __ballot_sync(kFull, refuse);
+                if (vm == 0u) {
+                    acc |= rem;
+                    break;
+                }
+                const int j = __ffs(vm) - 1;
+                acc |= rem & ((1u << j) - 1u);
+                R += __shfl_sync(kFull, dk, j);
+                rem &= ~((2u << j) - 1u);
+            }
+            if (em != 0u) E += __shfl_sync(kFull, Pk, 31 - __clz(em)) - R;
+            if (lane == 0) stg.accmask[g] = acc;
+        }
+        bar_arrive(5 + s, NT);
+    }
+    if (lane == 0) sm.st.E_fx = E;
+}
+
 // One pass over the selected classes (mu = 0..3, parity 0,1).  Heat-bath:
 // class by class over the whole lattice.  Overrelaxation: slab by slab of the
 // last coordinate (x3 = t, the h range [t S, (t+1) S) of every class array,
 // S = L^3 / 2) and the classes within each slab.
 template <int NWP, bool FAST>
 __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t tag, int B,
-                         int class_mask)
+                         int class_mask, const KernelArgs *muca = nullptr)
 {
     constexpr int CH = NWP * 32;
     if (threadIdx.x == 0) sm.acc_cnt = 0ull;
@@ -588,7 +664,10 @@ __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t
             if (!((class_mask >> cls) & 1)) continue;
             const int mu = cls >> 1, p = cls & 1;
             if (consumer) {
-                consume_class<NWP>(sm, B, nchunk);
+                if (kind == 2)
+                    consume_class_muca<NWP>(sm, nchunk, mu, p, *muca);
+                else
+                    consume_class<NWP>(sm, B, nchunk);
             } else {
                 switch (mu) {
                     case 0: produce_class<0, NWP, FAST>(sm, th, p, a_f, tag, B, 0, half, nchunk); break;
@@ -603,7 +682,7 @@ __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t
     if (threadIdx.x == 0) {
         const unsigned long long n =
             (unsigned long long)__popc(class_mask & 0xFF) * (unsigned long long)half;
-        if (kind == 0) {
+        if (kind != 1) {
             sm.st.hb_acc += sm.acc_cnt;
             sm.st.hb_tot += n;
         } else {
@@ -762,7 +841,8 @@ __global__ void __launch_bounds__((NWP + 1) * 32, min_ctas<NWP>()) llr_kernel(Ke
 {
     __shared__ Smem<NWP> sm;
     const int tid = threadIdx.x;
-    const bool multi = args.program == kProgSweeps || args.program == kProgRM;
+    const bool multi =
+        args.program == kProgSweeps || args.program == kProgRM || args.program == kProgMuca;
     const int per_lat = multi ? args.n_therm + args.n_meas : 1;
     const unsigned n_items = (unsigned)args.n_lat * (unsigned)per_lat;
     unsigned *counter = args.sync;
@@ -855,8 +935,25 @@ __global__ void __launch_bounds__((NWP + 1) * 32, min_ctas<NWP>()) llr_kernel(Ke
             case kProgPass: {
                 if (tid == 0 && args.a_in) sm.st.a = args.a_in[lat];
                 __syncthreads();
-                run_pass<NWP, FAST>(sm, th, args.pass_kind, (float)sm.st.a, kTagSweep,
-                                    args.block, args.class_mask);
+                if (args.pass_kind == 2)   // multicanonical heat-bath pass at slope a0
+                    run_pass<NWP, FAST>(sm, th, 2, (float)args.muca_a0, kTagSweep, 1,
+                                        args.class_mask, &args);
+                else
+                    run_pass<NWP, FAST>(sm, th, args.pass_kind, (float)sm.st.a, kTagSweep,
+                                        args.block, args.class_mask);
+                break;
+            }
+            case kProgMuca: {
+                // one multicanonical composite sweep (Sec. 2.6): heat-bath pass
+                // for the weight 1/rho~, n_or overrelaxation passes (they keep
+                // E, so every weight of E takes them), resync, energy history
+                run_pass<NWP, FAST>(sm, th, 2, (float)args.muca_a0, kTagSweep, 1, 0xFF, &args);
+                for (int k = 0; k < args.n_or; ++k)
+                    run_pass<NWP, FAST>(sm, th, 1, 0.0f, kTagSweep, 1, 0xFF);
+                end_of_sweep<NWP>(sm, th, false);
+                if (tid == 0 && args.e_hist)
+                    args.e_hist[(size_t)j * (size_t)args.n_lat + (size_t)lat] =
+                        (double)sm.st.E_fx * kInvFx;
                 break;
             }
             case kProgBegin: {
@@ -1005,7 +1102,7 @@ int resident_ctas()
 template <int NWP, bool FAST>
 cudaError_t launch_t(const KernelArgs &a, cudaStream_t s)
 {
-    const bool multi = a.program == kProgSweeps || a.program == kProgRM;
+    const bool multi = a.program == kProgSweeps || a.program == kProgRM || a.program == kProgMuca;
     const long long items = (long long)a.n_lat * (multi ? (a.n_therm + a.n_meas) : 1);
     if (items <= 0) return cudaSuccess;
     const long long cap = resident_ctas<NWP, FAST>();

@@ -72,6 +72,7 @@ __device__ __forceinline__ long long dist_fx(long long E, long long lo, long lon
 
 // Philox counter word 2 ("tag") of each kind of draw.
 constexpr uint32_t kTagSweep = 0u;
+constexpr uint32_t kTagMuca = 12u;       // the multicanonical accept draw of a link
 constexpr uint32_t kTagApproach = 14u;
 constexpr uint32_t kTagInit = 15u;
 constexpr int kSamplerMaxAttempts = 64;

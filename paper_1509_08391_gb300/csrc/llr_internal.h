@@ -21,6 +21,7 @@ enum Program : int {
     kProgBegin = 5,     // plain form: take a from a_in, clear the measurement
     kProgFinish = 6,    // plain form: resync + optional measurement + sweep counter
     kProgUpdate = 7,    // plain form: Robbins-Monro update from the accumulated measurement
+    kProgMuca = 8,      // multicanonical composite sweeps (weight 1/rho~), energy history
 };
 
 struct KernelArgs {
@@ -47,6 +48,13 @@ struct KernelArgs {
     // graph replays: the Robbins-Monro step number lives in device memory
     const int *step_dev;  // nullable: rm_index += *step_dev, history row *step_dev
     double *hist;         // nullable: hist[step * n_lat + lattice] = new a
+    // multicanonical weight 1/rho~ (pass kind 2 and kProgMuca): ln rho~ at the
+    // edges e0 + k de (muca_n + 1 values) and the slope of each interval
+    const double *muca_lnr;
+    const double *muca_a;
+    int muca_n;
+    double muca_e0, muca_de, muca_a0;
+    double *e_hist;       // kProgMuca, nullable: e_hist[sweep * n_lat + lattice] = E
 };
 
 // *step += 1 (the last node of a captured Robbins-Monro step).

@@ -31,7 +31,7 @@ EXPORTS = [
     "llr_mlp_create", "llr_mlp_num_params", "llr_mlp_get_params", "llr_mlp_set_params",
     "llr_mlp_set_norm", "llr_mlp_get_norm", "llr_mlp_predict", "llr_mlp_grad", "llr_mlp_fit",
     "llr_mlp_destroy", "llr_set_wait_limit", "llr_state_bytes", "llr_save_state",
-    "llr_load_state", "llr_replica_exchange",
+    "llr_load_state", "llr_replica_exchange", "llr_set_muca_weight", "llr_muca_sweep",
 ]
 NOALLOC_MAX_CENTRES = 65536
 
@@ -108,6 +108,8 @@ def load(path: str = LIB_PATH):
         "llr_save_state": [P, P],
         "llr_load_state": [P, P],
         "llr_replica_exchange": [P, I, P, P, U32, P],
+        "llr_set_muca_weight": [P, I, D, D, P, D],
+        "llr_muca_sweep": [P, I, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -241,6 +243,20 @@ class Batch:
         _check(load().llr_replica_exchange(self._h, pr.size // 2, _ptr(pr), _ptr(a),
                                            int(round_) & 0xFFFFFFFF, _ptr(acc)))
         return acc[:pr.size // 2].astype(bool)
+
+    def set_muca_weight(self, e0, de, a, a0):
+        """The multicanonical weight 1/rho~ (llr_set_muca_weight)."""
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        _check(load().llr_set_muca_weight(self._h, a.size, float(e0), float(de), _ptr(a),
+                                          float(a0)))
+
+    def muca_sweep(self, n_sweeps, history=True):
+        """n multicanonical composite sweeps; the energies after each sweep as
+        an (n_sweeps, n_lattices) array (or None)."""
+        out = np.zeros((int(n_sweeps), self.n)) if history else None
+        _check(load().llr_muca_sweep(self._h, int(n_sweeps),
+                                     _ptr(out) if out is not None else None))
+        return out
 
     # ------------------------------------------------------------ inspection
     def energy(self):
