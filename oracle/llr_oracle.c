@@ -25,7 +25,7 @@
  *   - Sec. 2.2, eq. kk21: a <- a + 12 <<dE>> / (dE^2 (n+1)) (sign of kk21;
  *     Algorithm 1 prints the opposite sign, see the readings below).
  *
- * Readings where the paper is silent (each one is also listed in the design doc):
+ * Readings where the paper is silent:
  *   R1 update scheme: the paper names only "an importance sampling
  *      algorithm for one sweep" (Algorithm 1) and mentions heat-bath and
  *      Metropolis.  A composite sweep here is one heat-bath pass followed by

@@ -166,26 +166,26 @@ class CompareResult:
 
 
 def compare(target: workloads.Workload, net, eps, n_rm, n_therm, n_meas, eps_stop=1e-4, hold=3,
-            judge_factor=2, stream=None):
+            ref_factor=2, stream=None):
     """Naive plain-schedule start versus learned warm start at the target volume."""
     L, e6v, d6v = interval_features(target)
     a_warm = net.predict(L, e6v, d6v)
     n0 = gain_offset(float(np.median(target.dE)), n_meas, eps, n_rm)
     a_naive = np.full(target.n_lattices, target.a0)
     with llr.Batch.from_workload(target, stream=stream, max_approach=1000) as b:
-        h_naive, t_naive = run_rm(b, a_naive, n_therm, n_meas, judge_factor * n_rm)
+        h_naive, t_naive = run_rm(b, a_naive, n_therm, n_meas, ref_factor * n_rm)
     with llr.Batch.from_workload(target, stream=stream, max_approach=1000) as b:
         h_warm, t_warm = run_rm(b, a_warm, n_therm, n_meas, n_rm, rm_offset=n0)
     _, m_naive = replica_mean_history(target, np.vstack([a_naive[None, :], h_naive]))
     _, m_warm = replica_mean_history(target, np.vstack([a_warm[None, :], h_warm]))
-    # judge: the long plain run's final replica means and errors
-    _, judge, jerr, _ = slopes_by_interval(target, h_naive[-1])
+    # reference: the long plain run's final replica means and errors
+    _, ref_a, jerr, _ = slopes_by_interval(target, h_naive[-1])
     _, aw, werr, _ = slopes_by_interval(target, h_warm[-1])
     _, an, nerr, _ = slopes_by_interval(target, h_naive[n_rm - 1])
-    agree_w = np.abs(aw - judge) <= 3.0 * np.sqrt(werr ** 2 + jerr ** 2) + 1e-12
-    agree_n = np.abs(an - judge) <= 3.0 * np.sqrt(nerr ** 2 + jerr ** 2) + 1e-12
-    err_n = np.abs(m_naive[:n_rm + 1] - judge[None, :]).mean(axis=1)
-    err_w = np.abs(m_warm - judge[None, :]).mean(axis=1)
+    agree_w = np.abs(aw - ref_a) <= 3.0 * np.sqrt(werr ** 2 + jerr ** 2) + 1e-12
+    agree_n = np.abs(an - ref_a) <= 3.0 * np.sqrt(nerr ** 2 + jerr ** 2) + 1e-12
+    err_n = np.abs(m_naive[:n_rm + 1] - ref_a[None, :]).mean(axis=1)
+    err_w = np.abs(m_warm - ref_a[None, :]).mean(axis=1)
     return CompareResult(converged_step(m_naive[:n_rm + 1], eps_stop, hold),
                          converged_step(m_warm, eps_stop, hold), agree_n, agree_w,
                          t_warm / n_rm, n0, eps, err_n, err_w)
