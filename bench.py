@@ -64,6 +64,10 @@ def parse():
                         "discretisation study (C_V peak against dE^2, Sec. 3.5)")
     p.add_argument("--phys-save", default="", help="write the final slopes a[replica][interval] "
                                                     "to this .npy file")
+    p.add_argument("--exchange", action="store_true",
+                   help="replica exchange at the paper's L = 8 range (Sec. 2.5): half-overlapping "
+                        "windows, one exchange round after every Robbins-Monro step; beta_c and "
+                        "the C_V peak against the paper, exchange rates")
     p.add_argument("--muca", action="store_true",
                    help="multicanonical check of Sec. 2.6 at L = 8: LLR slopes of a coarse volume "
                         "study, then chains with the weight 1/rho~: histogram flatness, round "
@@ -564,6 +568,73 @@ def lnrho_table(e0, de, a, E):
     return lnr[k] + np.asarray(a)[k] * (E - (e0 + k * de))
 
 
+def run_exchange(args):
+    """--exchange: the LLR run of the paper's L = 8 range with overlapping
+    intervals and replica exchange (Sec. 2.5): 511 windows of width 2 d,
+    d = (E_max - E_min) / 512, lower edges d apart, 8 replicas; after every
+    Robbins-Monro step one exchange round over the neighbouring windows of
+    alternating parity (llr_replica_exchange).  Per replica the slopes at the
+    window centres give ln rho~ and the C_V peak."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1509_08391_gb300 import build as bld
+    bld.build()
+    from paper_1509_08391_gb300 import llr, workloads
+    L, R = 8, args.phys_replicas
+    e_lo, e_hi, _, n_rm = workloads.PAPER_VOLUME_STUDY[L]
+    six_v = 6.0 * L ** 4
+    d = six_v * (e_hi - e_lo) / 512
+    n_win = 511
+    E = workloads.place_intervals(L, n_win, e_lo, e_hi, 2 * d)
+    Ls, lo, de, iid, rid = [], [], [], [], []
+    for k in range(n_win):
+        for r in range(R):
+            Ls.append(L)
+            lo.append(float(E[k]))
+            de.append(2 * d)
+            iid.append(k)
+            rid.append(r)
+    w = workloads.Workload("u1_4d_L8_511win_overlap_x%d" % R, Ls, lo, de, iid, rid,
+                           workloads.SEED_BASE + 30, n_therm=args.phys_therm,
+                           n_meas=args.phys_meas, n_rm=n_rm)
+    n = w.n_lattices
+    t0 = time.perf_counter()
+    tried = taken = 0
+    with llr.Batch.from_workload(w, max_approach=5000) as b:
+        a = np.full(n, w.a0)
+        t_ex = 0.0
+        for step in range(n_rm):
+            a, _ = b.rm_step(a, w.n_therm, w.n_meas, step)
+            te = time.perf_counter()
+            acc = b.replica_exchange(workloads.exchange_pairs(w, step), a, step)
+            t_ex += time.perf_counter() - te
+            tried += acc.size
+            taken += int(acc.sum())
+        ok = bool(np.all(b.status() == 0))
+    t_run = time.perf_counter() - t0
+    rid = np.asarray(rid)
+    bc, cv = [], []
+    centres = E + d
+    for r in range(R):
+        idx = np.nonzero(rid == r)[0]
+        b_r, v_r = llr.cv_peak(centres, a[idx], 1.0, 1.016, n_grid=1601, tol=1e-10)
+        bc.append(b_r)
+        cv.append(v_r / six_v ** 2)
+    bc, cv = np.array(bc), np.array(cv)
+    out = {"metric": "LLR with replica exchange (Sec. 2.5) at L = 8", "L": L, "windows": n_win,
+           "window_width": 2 * d, "spacing": d, "replicas": R, "n_therm": w.n_therm,
+           "n_meas": w.n_meas, "n_rm": n_rm, "status_ok": ok,
+           "exchange": {"pairs_tried": tried, "exchanged": taken,
+                        "rate": taken / max(tried, 1), "seconds": t_ex},
+           "beta_c": {"mean": float(bc.mean()), "stderr": float(bc.std(ddof=1) / np.sqrt(R)),
+                      "paper": PAPER_BETA_C[L]},
+           "cv_peak": {"mean": float(cv.mean()), "stderr": float(cv.std(ddof=1) / np.sqrt(R)),
+                       "paper": PAPER_CV_PEAK[L]},
+           "beta_c_per_replica": bc.tolist(), "cv_peak_per_replica": cv.tolist(),
+           "wall_seconds": t_run}
+    print(json.dumps(out), flush=True)
+
+
 def run_muca(args):
     """--muca: the ergodicity check of Sec. 2.6 at L = 8.  (1) LLR slopes of
     the paper's L = 8 range in 64 intervals (4 replicas, 300 Robbins-Monro
@@ -701,6 +772,9 @@ def main():
         return
     if args.muca:
         run_muca(args)
+        return
+    if args.exchange:
+        run_exchange(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
