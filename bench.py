@@ -72,6 +72,10 @@ def parse():
                    help="multicanonical check of Sec. 2.6 at L = 8: LLR slopes of a coarse volume "
                         "study, then chains with the weight 1/rho~: histogram flatness, round "
                         "trips, reweighted <E> and C_V peak against the LLR reconstruction")
+    p.add_argument("--muca-L", type=int, default=8)
+    p.add_argument("--muca-slopes", default="",
+                   help="take the LLR slopes from a --phys-save file (row 0 the interval "
+                        "centres, then one row per replica) instead of a coarse LLR run")
     p.add_argument("--muca-chains", type=int, default=512)
     p.add_argument("--muca-sweeps", type=int, default=4000)
     p.add_argument("--phases", action="store_true",
@@ -559,6 +563,16 @@ def run_discretisation(args, L, n_list):
     print(json.dumps(out), flush=True)
 
 
+# <E>/6V at L = 12 from the paper's comparison of LLR and reweighting with
+# rho~ (the table beside Fig. plaq_comp): beta -> (LLR, reweighting), errors.
+PAPER_E_L12 = {1.006: ((0.60180, 6e-5), (0.601714, 8e-6)),
+               1.008: ((0.60901, 8e-5), (0.60906, 1e-5)),
+               1.010: ((0.6271, 4e-4), (0.6274, 1e-4)),
+               1.01023: ((0.6349, 5e-4), (0.6352, 1e-4)),
+               1.012: ((0.65685, 5e-5), (0.65687, 1e-5)),
+               1.014: ((0.66018, 4e-5), (0.660230, 5e-6))}
+
+
 def lnrho_table(e0, de, a, E):
     """ln rho~ of eq. rhoguess at energies E (numpy, for the analysis of the
     multicanonical samples): 0 at e0, slope a[k] in interval k, the end slopes
@@ -648,26 +662,36 @@ def run_muca(args):
     from paper_1509_08391_gb300 import build as bld
     bld.build()
     from paper_1509_08391_gb300 import llr, workloads
-    L, n_int = 8, 64
+    L, n_int = args.muca_L, 64
     six_v = 6.0 * L ** 4
     t_all = time.perf_counter()
-    w = workloads.paper_volume_study(L, replicas=4, n_therm=5, n_meas=20, n_rm=300, n_int=n_int)
     stream = torch.cuda.Stream()
-    with llr.Batch.from_workload(w, stream=stream.cuda_stream, max_approach=5000) as b:
-        a_dev = torch.full((w.n_lattices,), w.a0, dtype=torch.float64, device="cuda")
-        b.rm_run(a_dev, w.n_therm, w.n_meas, 0, w.n_rm)
-        torch.cuda.synchronize()
-        a = a_dev.cpu().numpy()
-    iid = np.asarray(w.interval_id)
-    uniq = np.unique(iid)
-    a_k = np.array([a[iid == k].mean() for k in uniq])
-    lo = np.array([w.E_lo[np.nonzero(iid == k)[0][0]] for k in uniq])
-    dE = w.dE[0]
-    e_min, e_max = lo[0], lo[-1] + dE
-    centres = lo + 0.5 * dE
+    llr_info = {}
+    if args.muca_slopes:
+        tab = np.load(args.muca_slopes)
+        centres, a_k = tab[0], tab[1:].mean(axis=0)
+        n_int = centres.size
+        dE = float(centres[1] - centres[0])
+        llr_info = {"slopes_from": "file", "replicas": int(tab.shape[0] - 1)}
+    else:
+        w = workloads.paper_volume_study(L, replicas=4, n_therm=5, n_meas=20, n_rm=300,
+                                         n_int=n_int)
+        with llr.Batch.from_workload(w, stream=stream.cuda_stream, max_approach=5000) as b:
+            a_dev = torch.full((w.n_lattices,), w.a0, dtype=torch.float64, device="cuda")
+            b.rm_run(a_dev, w.n_therm, w.n_meas, 0, w.n_rm)
+            torch.cuda.synchronize()
+            a = a_dev.cpu().numpy()
+        iid = np.asarray(w.interval_id)
+        uniq = np.unique(iid)
+        a_k = np.array([a[iid == k].mean() for k in uniq])
+        lo = np.array([w.E_lo[np.nonzero(iid == k)[0][0]] for k in uniq])
+        dE = w.dE[0]
+        centres = lo + 0.5 * dE
+        llr_info = {"replicas": 4, "n_rm": w.n_rm}
+    e_min, e_max = centres[0] - 0.5 * dE, centres[-1] + 0.5 * dE
     # multicanonical chains: hot start, approach into [E_min, E_max], then W = 1/rho~
     nc = args.muca_chains
-    wm = workloads.Workload("u1_4d_L8_muca_x%d" % nc, [L] * nc, [e_min] * nc, [e_max - e_min] * nc,
+    wm = workloads.Workload("u1_4d_L%d_muca_x%d" % (L, nc), [L] * nc, [e_min] * nc, [e_max - e_min] * nc,
                             list(range(nc)), [0] * nc, workloads.SEED_BASE + 40)
     a0 = float(a_k.mean())
     t0 = time.perf_counter()
@@ -723,8 +747,8 @@ def run_muca(args):
     E_mu_c = moments(b_llr, x, lr)[0] / six_v
     _, E1, _ = llr.observables(centres, a_k, [b_llr])
     out = {"metric": "multicanonical reweighting vs LLR reconstruction (Sec. 2.6)", "L": L,
-           "llr": {"intervals": n_int, "replicas": 4, "n_rm": w.n_rm, "dE": dE,
-                   "beta_c": b_llr, "cv_peak": cv_llr / six_v ** 2},
+           "llr": dict(llr_info, intervals=int(n_int), dE=dE, beta_c=b_llr,
+                       cv_peak=cv_llr / six_v ** 2),
            "muca": {"chains": nc, "sweeps": args.muca_sweeps, "a0": a0,
                     "heat_bath_acceptance": float(st["hb_acc"].sum() / st["hb_tot"].sum()),
                     "histogram_over_range": [float(f) for f in frac],
@@ -735,6 +759,20 @@ def run_muca(args):
            "E_over_6V_at_llr_beta_c": {"muca": E_mu_c, "llr": float(E1[0] / six_v)},
            "paper": {"beta_c": PAPER_BETA_C[L], "cv_peak": PAPER_CV_PEAK[L]},
            "wall_seconds": time.perf_counter() - t_all}
+    if L == 12:
+        # the paper's table beside Fig. plaq_comp: <E>/6V at six couplings
+        rows = []
+        bl = sorted(PAPER_E_L12)
+        _, E_llr, _ = llr.observables(centres, a_k, bl)
+        for bb, el in zip(bl, E_llr):
+            vals = [moments(bb, E[:, gidx].ravel(),
+                            lnrho_table(e_min, dE, a_k, E[:, gidx].ravel()))[0] / six_v
+                    for gidx in groups]
+            rows.append({"beta": bb, "muca": moments(bb, x, lr)[0] / six_v,
+                         "muca_err": float(np.std(vals, ddof=1) / np.sqrt(len(vals))),
+                         "llr_same_slopes": float(el / six_v),
+                         "paper_llr": PAPER_E_L12[bb][0], "paper_reweighting": PAPER_E_L12[bb][1]})
+        out["E_over_6V_table"] = rows
     print(json.dumps(out), flush=True)
 
 
