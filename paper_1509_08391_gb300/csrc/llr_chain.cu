@@ -28,13 +28,17 @@
 //     the von Mises proposal (Best & Fisher 1979), evaluate its dE from the
 //     stored new angle exactly as the old local energy is evaluated, convert
 //     dE to int64 fixed point (2^-32) and form warp prefix sums; a consumer
-//     warp walks the chunks in
-//     link order and decides each block of B links with the restricted
-//     Metropolis rule dist(E + dE_block) <= dist(E), using a ballot to find
-//     the first rejected block among 32 speculatively accepted ones, then
-//     writes the accepted angles.  Chunks pass through a 4-stage shared
-//     memory ring guarded by named barriers, so proposals for later chunks
-//     overlap with the scan of earlier ones.
+//     warp walks the chunks in link order and decides each block of B links
+//     with the restricted Metropolis rule dist(E + dE_block) <= dist(E),
+//     using a ballot to find the first rejected block among 32
+//     speculatively accepted ones, and publishes an accept mask per group;
+//     the producers write the accepted angles.  Chunks pass through a
+//     4-stage shared memory ring guarded by named barriers, so proposals for
+//     later chunks overlap with the scan of earlier ones.
+//   * The multicanonical pass (Sec. 2.6) has the same producers at a fixed
+//     proposal slope; its consumer replaces the window rule by a
+//     Metropolis-Hastings test for the weight 1/rho~ in the same
+//     speculative scan.
 //   * Overrelaxation (theta' = -theta - 2 alpha) conserves E exactly, so its
 //     passes skip the scan: every thread reflects links (neighbours read with
 //     plain loads) and writes them directly.
