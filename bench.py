@@ -167,11 +167,12 @@ def config_dict(args, w, world):
             "l2": "inputs larger than L2 (5.2 GB of links per GPU)"}
 
 
-def cpu_baseline(w, n_sweeps=8, max_lat=None):
+def cpu_baseline(w, n_sweeps=8, max_lat=None, threads=None):
     """The FP64 oracle on a bounded sample of the same workload (host cores):
-    one lattice per core, n_sweeps composite sweeps (about 10 s on 16 cores)."""
+    one lattice per core, n_sweeps composite sweeps (about 10 s on 16 cores);
+    threads=1 gives the one-core figure."""
     import oracle
-    cores = os.cpu_count() or 1
+    cores = (os.cpu_count() or 1) if threads is None else threads
     n = min(cores, w.n_lattices) if max_lat is None else max_lat
     g = oracle.Geom([20] * 4)
     lats = [oracle.Lattice(g, w.seed, w.interval_id[i], w.replica_id[i], w.E_lo[i], w.dE[i],
@@ -326,6 +327,23 @@ def run_ours(args, rank, world, local_rank):
     orr = float(st["or_acc"].sum() / max(st["or_tot"].sum(), 1))
     drift = float(st["max_drift"].max())
     status_ok = bool(np.all(b.status() == 0))
+    # heat-bath and overrelaxation passes of the whole batch, each timed as its
+    # own launch (outside the timed region): link updates/s per pass kind
+    a_pass = a_dev.cpu().numpy()
+    pass_rates = {}
+    for kind, name in ((0, "heat_bath"), (1, "overrelaxation")):
+        b.single_pass(kind, a_pass)              # warm-up
+        t_ms = []
+        for _ in range(3):
+            p0 = torch.cuda.Event(enable_timing=True)
+            p1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            p0.record(stream)
+            b.single_pass(kind, a_pass)
+            p1.record(stream)
+            p1.synchronize()
+            t_ms.append(p0.elapsed_time(p1))
+        pass_rates[name] = n * 4 * 20 ** 4 / (min(t_ms) / 1e3)
     b.close()
     if rank != 0:
         return
@@ -333,7 +351,8 @@ def run_ours(args, rank, world, local_rank):
     # roofline of the dominant kernel (the batched sweep kernel, one launch per step)
     upd_per_launch = upd_per_step
     mhz = clk.get("sm_max_mhz") or 2070.0
-    peak_sfu = SFU_OPS_PER_CLK_SM * 152 * mhz * 1e6 / 1e9               # G MUFU ops/s
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_sfu = SFU_OPS_PER_CLK_SM * n_sm * mhz * 1e6 / 1e9              # G MUFU ops/s
     ach_sfu = MUFU_PER_UPDATE * upd_per_launch / (per_launch_ms / 1e3) / 1e9
     hbm_peak, hbm_src = 6800.0, "fallback (6.8 TB/s, no measured peaks file)"
     try:
@@ -349,15 +368,19 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64",
         "data": "synthetic (hot start from Philox, seed %d)" % w.seed,
         "config": config_dict(args, w, world),
-        "rm_intervals_per_s": world * args.intervals * 8 / (per_launch_ms / 1e3),
+        "rm_lattice_steps_per_s": world * n / (per_launch_ms / 1e3),
+        "rm_lattice_steps_note": "Robbins-Monro steps of (interval, replica) chains per second "
+                                 "(one step = n_therm + n_meas composite sweeps and the update)",
+        "link_updates_per_s_by_pass": pass_rates,
         "acceptance": {"heat_bath": hb, "overrelaxation": orr},
         "max_tracked_minus_fresh": drift, "status_ok": status_ok,
         "roofline": {"bound": "alu", "achieved": ach_sfu, "peak": peak_sfu,
                      "unit": "G MUFU ops/s (SFU pipe)", "frac": ach_sfu / peak_sfu,
                      "traffic": traffic,
                      "algorithmic": "12 MUFU ops per link update (sine and cosine of 6 staples)",
-                     "peak_source": "16 MUFU ops/clk/SM x 152 SMs x %.0f MHz (derived from "
-                                    "unit counts and the sampled max clock)" % mhz},
+                     "peak_source": "16 MUFU ops/clk/SM x %d SMs x %.0f MHz (derived from "
+                                    "unit counts, the queried SM count and the sampled max "
+                                    "clock)" % (n_sm, mhz)},
         "roofline_hbm": {"bound": "hbm", "achieved": ach_hbm, "peak": hbm_peak, "unit": "GB/s",
                          "frac": ach_hbm / hbm_peak, "peak_source": hbm_src},
         "clocks": clk, "gpu_launches": args.steps,
@@ -366,6 +389,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_cpu:
         try:
             out["cpu_baseline"], _ = cpu_baseline(w)
+            out["cpu_baseline_1core"], _ = cpu_baseline(w, n_sweeps=1, max_lat=1, threads=1)
         except Exception as e:  # keep the GPU line even if the host baseline fails
             out["cpu_baseline"] = {"error": str(e)}
     print(json.dumps(out), flush=True)

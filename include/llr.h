@@ -83,6 +83,13 @@ int llr_approach(llr_handle h, int max_sweeps, int *sweeps_out);
  * each one heat-bath pass plus n_or overrelaxation passes restricted to the
  * window (Sec. 2.4: the importance-sampling update of Algorithm 1 with the
  * window imposed after the proposal), followed by a fresh plaquette sum.
+ * Window rule, applied block by block in link order to the running energy
+ * E (int64 fixed point, 2^-32, fed by the float32 dE of every move): a
+ * heat-bath block is taken iff dist(E + dE) <= dist(E), dist the distance
+ * from the closed window; an overrelaxation block (a reflection, which keeps
+ * E in exact arithmetic) is taken iff E + dE lies in the window or E does
+ * not, and a reflection with |dE| > 2^-14 is refused.  Inside the window both
+ * are the indicator of eq. kk7.
  * If measure != 0, dE_sum_out (host double[n_lattices], nullable) receives
  * the sum over these sweeps of E - E_lo - dE/2 (eq. kk10).  Synchronous. */
 int llr_sweep(llr_handle h, const double *a, int n_sweeps, int measure, double *dE_sum_out);
@@ -94,7 +101,11 @@ int llr_sweep(llr_handle h, const double *a, int n_sweeps, int measure, double *
  * ignored; needs llr_set_muca_weight).  Each selected checkerboard class (bit c of class_mask selects
  * class c = 2 mu + parity; 0xFF = the whole pass, in class order) draws its
  * proposals and accepts them in link order with the window rule of
- * llr_sweep.  Synchronous. */
+ * llr_sweep.  kind 3 = the end of a composite sweep: the running energy is
+ * re-synchronised with the fresh plaquette sum and the sweep counter
+ * advances (a and class_mask ignored), so heat-bath classes, overrelaxation
+ * passes and kind 3 in the order of llr_sweep reproduce its sweeps bit for
+ * bit.  Synchronous. */
 int llr_pass(llr_handle h, int kind, const double *a, int class_mask);
 
 /* One Robbins-Monro iteration for every lattice (Algorithm 1, eq. kk21):
@@ -109,7 +120,8 @@ int llr_rm_step(llr_handle h, int n_therm, int n_meas, int rm_index, double *a_i
 /* The same iteration with device buffers and no synchronisation: a_in and
  * a_out (may alias) and dE_mean_out (nullable) are device double[n_lattices].
  * All lattices advance in one launch on the handle's stream, so the call can
- * be captured in a CUDA graph.  Check llr_status afterwards. */
+ * be captured in a CUDA graph.  A bounded wait that runs out is reported by
+ * the next llr_status (or any other synchronous call on the handle). */
 int llr_rm_step_dev(llr_handle h, int n_therm, int n_meas, int rm_index, const double *a_in,
                     double *a_out, double *dE_mean_out);
 
@@ -120,7 +132,9 @@ int llr_rm_step_dev(llr_handle h, int n_therm, int n_meas, int rm_index, const d
  * in, a^(n + n_steps) out; hist_dev: device double[n_steps][n_lattices] of
  * a after each step, or NULL.  Asynchronous on the handle's stream.  The
  * graph is captured on the first call and reused while the arguments stay
- * the same. */
+ * the same.  A bounded wait that runs out in any replay is reported by the
+ * next llr_status (or any other synchronous call on the handle); once one has
+ * run out, the remaining sweeps of every replay that would wait skip at once. */
 int llr_rm_run(llr_handle h, int n_therm, int n_meas, int rm_index0, int n_steps, double *a_dev,
                double *hist_dev);
 
@@ -197,8 +211,10 @@ int llr_set_sweep_counter(llr_handle h, int lattice, uint32_t value);
 int llr_stats(llr_handle h, double *out, int reset);
 
 /* Per-lattice status words (0 = fine); host int[n_lattices].  Returns
- * LLR_ERR_TIMEOUT if, in the last batched launch, a bounded device wait for a
- * lattice's previous sweep ran out (that lattice was then left unchanged). */
+ * LLR_ERR_TIMEOUT if, in any batched launch since the last synchronous call,
+ * a bounded device wait for a lattice's previous sweep ran out (that sweep
+ * and the later ones of the launch that would have waited were skipped);
+ * reading it clears it. */
 int llr_status(llr_handle h, int *out);
 
 /* Reconstruction of ln rho at the interval centres by the trapezium rule
@@ -230,8 +246,11 @@ int llr_observables(int n, const double *centres, const double *a, int n_beta,
  *     cudaStream_t or NULL.  The call only enqueues work on that stream.
  *   Errors: LLR_ERR_ARG if n is outside 1..LLR_NOALLOC_MAX_CENTRES or a
  *     pointer is NULL; LLR_ERR_CUDA if the set-up or a launch fails.
- * The first call on a device looks up the device address of the array (with
- * that device current), so make that first call before any stream capture.
+ * Every call looks up the device address of the array in the current
+ * device's context (cudaGetSymbolAddress, with that device current).  The
+ * first call on a device may be the one that loads this library's device
+ * code there, which is when the 512 KiB array is allocated by the CUDA
+ * runtime; make that first call before any stream capture.
  * Every call reuses the same array and leaves its last contents there; calls
  * whose work overlaps on the GPU (different streams, or different host
  * threads on one device) race on it and must be serialised by the caller. */

@@ -73,6 +73,7 @@ def lib():
                 "orc_lat_stats": (None, [P, dp]),
                 "orc_lat_hot_start": (None, [P]),
                 "orc_vonmises": (I, [D, up, U32, U32, U32, dp]),
+                "orc_vonmises_attempts": (I, [D, up, U32, U32, U32, I, dp, dp, dp]),
                 "orc_lat_sweep": (None, [P, D, I]),
                 "orc_lat_pass": (None, [P, I, D]),
                 "orc_lat_class_pass": (None, [P, I, I, D]),
@@ -131,6 +132,15 @@ def vonmises(kappa, key, c0, c1, c2):
     x = ctypes.c_double(0.0)
     att = lib().orc_vonmises(float(kappa), _up(k), c0, c1, c2, ctypes.byref(x))
     return x.value, att
+
+
+def vonmises_attempts(kappa, key, c0, c1, c2, n_max=8):
+    """Every sampler attempt: (X if taken, margin m1, margin m2) arrays."""
+    k = np.asarray(key, dtype=np.uint32).copy()
+    X, m1, m2 = np.zeros(n_max), np.zeros(n_max), np.zeros(n_max)
+    n = lib().orc_vonmises_attempts(float(kappa), _up(k), c0, c1, c2, int(n_max), _dp(X),
+                                    _dp(m1), _dp(m2))
+    return X[:n], m1[:n], m2[:n]
 
 
 class Geom:

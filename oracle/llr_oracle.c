@@ -42,11 +42,17 @@
  *      or the overrelaxation reflection); the proposals are then accepted
  *      or rejected in ascending site order, in blocks of B consecutive
  *      links starting at the group's first link, by the Metropolis rule for
- *      the restricted measure: a block is
+ *      the restricted measure: a heat-bath block is
  *      accepted iff dist(E + dE_block) <= dist(E), where dist is the distance
  *      of E from the window (0 inside).  Inside the window this is exactly
  *      the indicator of eq. kk7; outside it only lets E move towards the
  *      window (used while approaching the window from a hot start).
+ *  R19 overrelaxation blocks: the reflection keeps E in exact arithmetic, so a
+ *      block is accepted iff E + dE_block lies in the window, or E does not
+ *      (outside the window reflections are always taken; in FP64 the dE of a
+ *      reflection, ~1e-15, is below the resolution of E and the dist rule
+ *      would take them too).  A reflection whose |dE| exceeds 2^-14 is
+ *      refused (a guard for float32 arithmetic; FP64 never reaches it).
  *   R3 heat-bath proposal: von Mises variate by Best & Fisher (1979).
  *   R4 random numbers: Philox4x32-10 (Salmon et al., SC'11), keyed by
  *      (seed, interval, replica), counter (link, sweep, tag, attempt / 2):
@@ -409,12 +415,64 @@ int orc_vonmises(double kappa, const uint32_t key[2], uint32_t c0, uint32_t c1, 
     return -1;
 }
 
+/* Every attempt of the sampler above, accepted or not (test diagnostics):
+ * for attempts 0 .. n_max-1, the variate X the attempt gives if it is taken,
+ * and the two margins of its accept test, m1 = c (2 - c) - u2 and
+ * m2 = ln(c / u2) + 1 - c (taken iff m1 > 0 or m2 >= 0).  A float32 sampler
+ * can take a different attempt than this FP64 one only where a margin is
+ * within its rounding of zero.  Returns the number of attempts written (0
+ * for the uniform proposal at |kappa| < 1e-6). */
+int orc_vonmises_attempts(double kappa, const uint32_t key[2], uint32_t c0, uint32_t c1,
+                          uint32_t c2, int n_max, double *X, double *m1, double *m2)
+{
+    if (fabs(kappa) < KAPPA_MIN) return 0;
+    double k = fabs(kappa);
+    double tau = 1.0 + sqrt(1.0 + 4.0 * k * k);
+    double rho = (tau - sqrt(2.0 * tau)) / (2.0 * k);
+    double r = (1.0 + rho * rho) / (2.0 * rho);
+    uint32_t w[4];
+    int n = n_max < SAMPLER_MAX_ATTEMPTS ? n_max : SAMPLER_MAX_ATTEMPTS;
+    for (int att = 0; att < n; ++att) {
+        if ((att & 1) == 0) {
+            uint32_t ctr[4] = {c0, c1, c2, (uint32_t)att >> 1};
+            orc_philox4x32_10(ctr, key, w);
+        }
+        uint32_t wa = w[2 * (att & 1)], wb = w[2 * (att & 1) + 1];
+        double u1 = orc_uniform(wa), u2 = orc_uniform(wb);
+        double z = cos(M_PI * u1);
+        double f = (1.0 + r * z) / (r + z);
+        double c = k * (r - f);
+        double x = (wa & 1u ? 1.0 : -1.0) * acos(f);
+        if (kappa < 0.0) x = wrap_angle(x + M_PI);
+        X[att] = x;
+        m1[att] = c * (2.0 - c) - u2;
+        m2[att] = log(c / u2) + 1.0 - c;
+    }
+    return n;
+}
+
 static double dist_to_window(double E, double lo, double hi)
 {
     if (E < lo) return lo - E;
     if (E > hi) return E - hi;
     return 0.0;
 }
+
+/* The window decision of one block of a group (R2, R19).  Heat-bath (mode
+ * 0): taken iff dist(E + d) <= dist(E).  Overrelaxation (mode 1): the
+ * reflection keeps E in exact arithmetic, so outside the window it is always
+ * taken and inside it is taken iff E + d stays inside.  Inside the window
+ * both are the indicator of eq. kk7. */
+static int block_taken(int mode, double E, double d, double lo, double hi)
+{
+    if (mode == 1) return dist_to_window(E, lo, hi) > 0.0 || dist_to_window(E + d, lo, hi) == 0.0;
+    return dist_to_window(E + d, lo, hi) <= dist_to_window(E, lo, hi);
+}
+
+/* Largest |dE| an overrelaxation move may carry (R19): 2^-14.  A reflection
+ * changes E only by rounding; a move beyond the bound is refused (a guard for
+ * float32 arithmetic that FP64 never reaches). */
+#define OR_DELTA_MAX 6.103515625e-05
 
 /* Index range of class cls's links (in update order) that lie in slab sl,
  * the sites whose last coordinate x_{d-1} equals sl.  The class lists are in
@@ -456,13 +514,14 @@ static void group_update(orc_lat *t, int c0, int c1, int mode, double a, uint32_
         }
         t->prop[l] = thn;
         t->dEl[l] = local_energy(n, phi, thn) - local_energy(n, phi, th);
+        if (mode == 1 && fabs(t->dEl[l]) > OR_DELTA_MAX) { t->prop[l] = th; t->dEl[l] = 0.0; }
     }
     /* sequential Metropolis accept in blocks of B links, update order */
     for (int b0 = c0; b0 < c1; b0 += t->block) {
         int b1 = b0 + t->block < c1 ? b0 + t->block : c1;
         double d = 0.0;
         for (int i = b0; i < b1; ++i) d += t->dEl[g->class_links[i]];
-        int acc = dist_to_window(t->E + d, lo, hi) <= dist_to_window(t->E, lo, hi);
+        int acc = block_taken(mode, t->E, d, lo, hi);
         if (acc) {
             for (int i = b0; i < b1; ++i) t->theta[g->class_links[i]] = t->prop[g->class_links[i]];
             t->E += d;
@@ -516,7 +575,7 @@ int orc_lat_class_trace(orc_lat *t, int cls, int mode, double a, double *th_old,
             int b1 = b0 + t->block < g1 ? b0 + t->block : g1;
             double d = 0.0;
             for (int i = b0; i < b1; ++i) d += t->dEl[g->class_links[i]];
-            int acc = dist_to_window(E + d, lo, hi) <= dist_to_window(E, lo, hi);
+            int acc = block_taken(mode, E, d, lo, hi);
             for (int i = b0; i < b1; ++i) {
                 th_prop[i - c0] = t->prop[g->class_links[i]];
                 E_before[i - c0] = E;

@@ -89,14 +89,19 @@ llr::KernelArgs base_args(llr_handle h)
     return a;
 }
 
-// Error word of the last persistent launch (nonzero: a bounded wait ran out).
+// Error word of the persistent launches since the last check (nonzero: a
+// bounded wait ran out in one of them); read and cleared.
 int check_queue(llr_handle h)
 {
     unsigned w = 0;
-    LLR_CUDA(cudaMemcpyAsync(&w, h->d_sync + 1, sizeof(unsigned), cudaMemcpyDeviceToHost,
+    LLR_CUDA(cudaMemcpyAsync(&w, h->d_sync, sizeof(unsigned), cudaMemcpyDeviceToHost,
                              h->stream));
     LLR_CUDA(cudaStreamSynchronize(h->stream));
-    if (w) return fail(LLR_ERR_TIMEOUT, "a lattice's previous sweep was not done in time");
+    if (w) {
+        LLR_CUDA(cudaMemsetAsync(h->d_sync, 0, sizeof(unsigned), h->stream));
+        LLR_CUDA(cudaStreamSynchronize(h->stream));
+        return fail(LLR_ERR_TIMEOUT, "a lattice's previous sweep was not done in time");
+    }
     return LLR_OK;
 }
 
@@ -206,6 +211,7 @@ int llr_init_lattice(llr_handle *out, const llr_config *cfg, void *cuda_stream)
     LLR_CUDA(cudaMalloc(&h->d_mean, sizeof(double) * (size_t)n));
     LLR_CUDA(cudaMalloc(&h->d_int, sizeof(int) * (size_t)(n + 1)));
     LLR_CUDA(cudaMalloc(&h->d_sync, sizeof(unsigned) * (size_t)(n + 2)));
+    LLR_CUDA(cudaMemset(h->d_sync, 0, sizeof(unsigned) * (size_t)(n + 2)));
     LLR_CUDA(cudaMalloc(&h->d_order, sizeof(int) * (size_t)n));
     LLR_CUDA(cudaMalloc(&h->d_step, sizeof(int)));
     {
@@ -240,6 +246,7 @@ int llr_approach(llr_handle h, int max_sweeps, int *sweeps_out)
                                  cudaMemcpyDeviceToHost, h->stream));
     std::vector<LatState> st;
     if (int r = pull_states(h, st)) return r;
+    if (int r = check_queue(h)) return r;
     for (int i = 0; i < h->n; ++i)
         if (st[(size_t)i].status == LLR_ERR_WINDOW)
             return fail(LLR_ERR_WINDOW, "lattice " + std::to_string(i) +
@@ -272,8 +279,9 @@ int llr_sweep(llr_handle h, const double *a_host, int n_sweeps, int measure, dou
 int llr_pass(llr_handle h, int kind, const double *a_host, int class_mask)
 {
     if (int r = check_handle(h)) return r;
-    if (kind < 0 || kind > 2)
-        return fail(LLR_ERR_ARG, "kind must be 0 (heat-bath), 1 (overrelaxation) or 2 (multicanonical)");
+    if (kind < 0 || kind > 3)
+        return fail(LLR_ERR_ARG, "kind must be 0 (heat-bath), 1 (overrelaxation), 2 "
+                                 "(multicanonical) or 3 (end of a composite sweep)");
     if (class_mask < 1 || class_mask > 0xFF) return fail(LLR_ERR_ARG, "class_mask must be in 1..255");
     if (kind == 0 && !a_host) return fail(LLR_ERR_ARG, "heat-bath pass needs a");
     if (kind == 2 && !h->d_muca) return fail(LLR_ERR_ARG, "no multicanonical weight set");
@@ -423,6 +431,7 @@ int llr_rm_step_plain(llr_handle h, int n_therm, int n_meas, int rm_index, doubl
         LLR_CUDA(cudaMemcpyAsync(dE_mean_out, h->d_mean, sizeof(double) * (size_t)h->n,
                                  cudaMemcpyDeviceToHost, h->stream));
     LLR_CUDA(cudaStreamSynchronize(h->stream));
+    if (int r = check_queue(h)) return r;
     for (int i = 0; i < h->n; ++i)
         if (!std::isfinite(a_inout[i]))
             return fail(LLR_ERR_NUMERIC, "non-finite a for lattice " + std::to_string(i));

@@ -270,6 +270,10 @@ struct Smem {
     LatState st;
     Stage<NWP> stage[kStages];
     long long red[NWP + 1];
+    // overrelaxation groups decided move by move: block-end / accept masks
+    // and the running energy
+    unsigned or_em[NWP + 1], or_acc[NWP + 1];
+    long long or_E;
     unsigned long long acc_cnt;
     unsigned long long cap_cnt;
     int item_lat, item_j, item_state;
@@ -427,12 +431,13 @@ __device__ __forceinline__ void staple_load(const float *th, int half, int L, co
     }
 }
 
-// Overrelaxation of one link from its 18 neighbour angles: the staples are
-// formed exactly as in staple_from, theta' = -theta - 2 alpha, alpha = arg S.
+// Staple sum of one link from its 18 neighbour angles, formed exactly as in
+// staple_from.
 template <bool FAST>
-__device__ __forceinline__ float reflect_from(const float v[18], float t0)
+__device__ __forceinline__ void staple_sum_regs(const float v[18], float &Sr, float &Si)
 {
-    float Sr = 0.0f, Si = 0.0f;
+    Sr = 0.0f;
+    Si = 0.0f;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const float pf = v[6 * j] - v[6 * j + 1] - v[6 * j + 2];
@@ -443,16 +448,59 @@ __device__ __forceinline__ float reflect_from(const float v[18], float t0)
         Sr += cf + cb;
         Si += sf + sb;
     }
-    return wrap_angle(-t0 - 2.0f * atan2f(Si, Sr));
 }
 
-// One overrelaxation group: the links of class (MU, p) with half-site index
-// in [h0, h0 + count).  theta' = -theta - 2 alpha keeps |S| cos(theta + alpha),
-// so E is unchanged in exact arithmetic and the move is always inside the
-// window; every link is written directly (the float32 rounding of E, ~1e-6
-// per link, is absorbed by the resync at the end of the composite sweep).
-// The neighbours are plain loads: within a slab they mostly hit L1/L2, and
-// with no consumer to feed the loads of many warps hide each other.
+// Largest |dE| of an overrelaxation move: 2^-14 (2^18 in the fixed point of
+// the running energy).  The reflection keeps the local energy
+// |S| cos(theta + alpha) exactly; a move changes E only through float32
+// rounding -- the reflection axis alpha carries the staple sum's error
+// (~1e-6 / |S|), the stored angle its rounding -- well below 2^-14 at
+// |S| <= 6.  A group of n moves therefore changes E by less than n * 2^-14,
+// and a group whose running energy is farther than that from both window
+// edges cannot have a move refused by the window rule.  In the groups that
+// are decided move by move, a move whose float32 dE estimate exceeds the
+// bound is refused (a guard never expected to act).
+constexpr float kOrDeltaMax = 6.103515625e-05f;   // 2^-14
+constexpr long long kOrDeltaMaxFx = 1ll << 18;
+constexpr int kOrRefused = (int)0x80000000;
+
+// theta' = -theta - 2 alpha of link theta_MU at half-site h of parity p, with
+// alpha = arg S (S from the 18 neighbour angles, plain loads); optionally the
+// float32 dE estimate in fixed point, evaluated like the heat-bath's: the local
+// energy Re(e^{i theta} S) at the stored new angle minus at the old one, same
+// staple sum, same sine/cosine (dfx = kOrRefused beyond the guard).
+template <int MU, bool FAST, bool WITH_DE>
+__device__ __forceinline__ float overrelax_link(const float *th, const float *own, int half, int L,
+                                                uint32_t magic, int p, int h, int &dfx)
+{
+    float va[18];
+    int x[4];
+    const int site = decode_half(h, p, L, magic, x);
+    staple_load<MU>(th, half, L, x, site, p, va);
+    const float t0 = own[h];
+    float Sr, Si;
+    staple_sum_regs<FAST>(va, Sr, Si);
+    const float tn = wrap_angle(-t0 - 2.0f * atan2f(Si, Sr));
+    if (WITH_DE) {
+        float sn, cn, so, co;
+        sin_cos<FAST>(tn, &sn, &cn);
+        sin_cos<FAST>(t0, &so, &co);
+        const float d = (cn * Sr - sn * Si) - (co * Sr - so * Si);
+        dfx = fabsf(d) <= kOrDeltaMax ? __float2int_rn(d * 4294967296.0f) : kOrRefused;
+    }
+    return tn;
+}
+
+// One overrelaxation group (the links of class (MU, p) with half-site index
+// in [h0, h0 + count)) whose running energy E is farther than count * 2^-14
+// from both window edges: E +- count 2^-14 lies inside the window (every move
+// is taken by the window rule) or entirely on one side outside it (outside,
+// reflections are always taken), so no decision depends on the moves' dE.
+// Every thread reflects its links and writes them directly; the running
+// energy is left as it is (the moves change E only by float32 rounding, which
+// the fresh energy at the end of the composite sweep takes up).  The
+// neighbours are plain loads: within a slab they mostly hit L1/L2, and with no
+// consumer to feed, the loads of many warps hide each other.
 template <int MU, int NWP, bool FAST>
 __device__ __noinline__ void overrelax_class(Smem<NWP> &sm, float *th, int p, int h0, int count)
 {
@@ -460,15 +508,162 @@ __device__ __noinline__ void overrelax_class(Smem<NWP> &sm, float *th, int p, in
     const int L = sm.st.L, half = sm.st.half;
     const uint32_t magic = sm.st.magic;
     float *own = th + (2 * MU + p) * half;
-    const int tid = threadIdx.x;
-    for (int local = tid; local < count; local += NT) {
-        float va[18];
-        int x[4];
-        const int site = decode_half(h0 + local, p, L, magic, x);
-        staple_load<MU>(th, half, L, x, site, p, va);
-        const float ta = own[h0 + local];
-        own[h0 + local] = reflect_from<FAST>(va, ta);
+    for (int local = threadIdx.x; local < count; local += NT) {
+        int dfx;
+        own[h0 + local] =
+            overrelax_link<MU, FAST, false>(th, own, half, L, magic, p, h0 + local, dfx);
     }
+}
+
+// Window decisions of one 32-link group in link order, by the calling warp.
+// Lane k holds Pk, the inclusive prefix sum of dE over the group's links
+// 0..k; em marks the lanes that end a block (blocks of B links start at
+// multiples of B).  Rules: heat-bath (OR_RULE false) takes a block iff
+// dist(E + dE_block) <= dist(E), dist the distance from the closed window;
+// overrelaxation (OR_RULE true) takes a block iff E + dE_block lies in the
+// window or E does not (outside, a reflection, which keeps E in exact
+// arithmetic, is always taken).  Inside the window both reduce to: taken iff
+// the energy after the block is inside.  Returns the mask of taken block
+// ends and advances E.
+template <bool OR_RULE>
+__device__ __forceinline__ unsigned window_scan_group(long long Pk, unsigned em, int B,
+                                                      long long &E, long long lo, long long hi)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned rem = em, acc = 0u;
+    // the sum of the block ending at this lane
+    const int bstart = lane & ~(B - 1);
+    const long long Pprev = __shfl_sync(kFull, Pk, bstart > 0 ? bstart - 1 : 0);
+    const long long bk = Pk - (bstart > 0 ? Pprev : 0ll);
+    if (em != 0u && E >= lo && E <= hi) {
+        // Inside the window (the usual case, and E stays inside): a block is
+        // taken iff lo - E <= Pk - R <= hi - E, R the sum of the blocks
+        // refused so far.  Keep the bounds rlo = lo - E + R, rhi = hi - E + R;
+        // a refusal at j adds its block sum bj.
+        long long rlo = lo - E, rhi = hi - E;
+        while (rem) {
+            const bool mine = (rem >> lane) & 1u;
+            const bool viol = mine && (Pk < rlo || Pk > rhi);
+            const unsigned vm = __ballot_sync(kFull, viol);
+            if (vm == 0u) {
+                acc |= rem;
+                break;
+            }
+            const int j = __ffs(vm) - 1;
+            acc |= rem & ((1u << j) - 1u);
+            const long long bj = __shfl_sync(kFull, bk, j);
+            rlo += bj;
+            rhi += bj;
+            rem &= ~((2u << j) - 1u);
+        }
+        // E after the group = E + P_last - R = lo + P_last - rlo
+        E = lo + __shfl_sync(kFull, Pk, 31 - __clz(em)) - rlo;
+    } else {
+        // Outside the window: every remaining block is decided as if the
+        // earlier ones were taken; the first refusal (one ballot) fixes the
+        // blocks before it, its dE is dropped and the rest is decided again.
+        long long base = 0;
+        while (rem) {
+            const long long Ea = E + (Pk - base);
+            const long long Eb = Ea - bk;
+            const bool mine = (rem >> lane) & 1u;
+            bool ok;
+            if (OR_RULE)
+                ok = dist_fx(Eb, lo, hi) > 0 || dist_fx(Ea, lo, hi) == 0;
+            else
+                ok = dist_fx(Ea, lo, hi) <= dist_fx(Eb, lo, hi);
+            const unsigned vm = __ballot_sync(kFull, mine && !ok);
+            if (vm == 0u) {
+                const int last = 31 - __clz(rem);
+                E += __shfl_sync(kFull, Pk, last) - base;
+                acc |= rem;
+                rem = 0u;
+            } else {
+                const int j = __ffs(vm) - 1;
+                acc |= rem & ((1u << j) - 1u);
+                const long long Pj = __shfl_sync(kFull, Pk, j);
+                const long long bj = __shfl_sync(kFull, bk, j);
+                E += (Pj - bj) - base;   // energy before the refused block
+                base = Pj;               // skip its contribution
+                rem &= ~((2u << j) - 1u);
+            }
+        }
+    }
+    return acc;
+}
+
+// One overrelaxation group whose running energy is within count * 2^-14 of a
+// window edge: the moves are decided in link order by the window rule on
+// their float32 dE estimates, which the running energy takes up.
+// Chunks of NT links: every thread forms its link's move and dE, the warps
+// form inclusive prefix sums; a chunk whose energy is at least NT * 2^-14 from
+// the edges is taken whole, otherwise warp 0 scans its 32-link groups in
+// order (window_scan_group) and the threads write the taken moves.  The
+// prefix sums are staged in the heat-bath's stage buffer (unused during an
+// overrelaxation pass).  The running energy enters and leaves in sm.or_E;
+// returns the number of moves this thread took.
+template <int MU, int NWP, bool FAST>
+__device__ __noinline__ int overrelax_class_scan(Smem<NWP> &sm, float *th, int p, int h0,
+                                                 int count, int B)
+{
+    constexpr int NT = (NWP + 1) * 32;
+    const int L = sm.st.L, half = sm.st.half;
+    const uint32_t magic = sm.st.magic;
+    const long long lo = sm.st.lo_fx, hi = sm.st.hi_fx;
+    float *own = th + (2 * MU + p) * half;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    long long *stP = reinterpret_cast<long long *>(g_stage_buf);
+    int taken = 0;
+    for (int c0 = 0; c0 < count; c0 += NT) {
+        const int local = c0 + tid;
+        const bool valid = local < count;
+        int dfx = 0;
+        float tn = 0.0f;
+        bool ok = false;
+        if (valid) {
+            tn = overrelax_link<MU, FAST, true>(th, own, half, L, magic, p, h0 + local, dfx);
+            ok = dfx != kOrRefused;
+            if (!ok) dfx = 0;
+        }
+        long long P = dfx;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(kFull, P, o);
+            if (lane >= o) P += y;
+        }
+        const bool isend = valid && (((lane & (B - 1)) == B - 1) || local == count - 1);
+        const unsigned em = __ballot_sync(kFull, isend);
+        stP[tid] = P;
+        if (lane == 0) sm.or_em[warp] = em;
+        __syncthreads();
+        if (warp == 0) {
+            long long E = sm.or_E;
+            const long long m = (long long)NT * kOrDeltaMaxFx;
+            const bool whole = (E - m >= lo && E + m <= hi) || E + m < lo || E - m > hi;
+            for (int g = 0; g <= NWP; ++g) {
+                const unsigned emg = sm.or_em[g];
+                const long long Pg = stP[g * 32 + lane];
+                unsigned acc;
+                if (whole) {
+                    acc = emg;
+                    if (emg) E += __shfl_sync(kFull, Pg, 31 - __clz(emg));
+                } else {
+                    acc = window_scan_group<true>(Pg, emg, B, E, lo, hi);
+                }
+                if (lane == 0) sm.or_acc[g] = acc;
+            }
+            if (lane == 0) sm.or_E = E;
+        }
+        __syncthreads();
+        if (valid && ok) {
+            const int eb = __ffs(em & ~((1u << lane) - 1u)) - 1;
+            if ((sm.or_acc[warp] >> eb) & 1u) {
+                own[h0 + local] = tn;
+                ++taken;
+            }
+        }
+    }
+    return taken;
 }
 
 // Consumer side: sequential Metropolis accept of the chunk's blocks in link
@@ -486,64 +681,8 @@ __device__ __noinline__ void consume_class(Smem<NWP> &sm, int B, int nchunk)
         bar_sync(1 + s, NT);
         Stage<NWP> &stg = sm.stage[s];
         for (int g = 0; g < NWP; ++g) {
-            const unsigned em = stg.endmask[g];
-            unsigned rem = em, acc = 0u;
-            const long long Pk = stg.P[g * 32 + lane];
-            // the sum of the block ending at this lane (blocks of B links
-            // start at multiples of B within the group)
-            const int bstart = lane & ~(B - 1);
-            const long long Pprev = __shfl_sync(kFull, Pk, bstart > 0 ? bstart - 1 : 0);
-            const long long bk = Pk - (bstart > 0 ? Pprev : 0ll);
-            if (em != 0u && E >= lo && E <= hi) {
-                // Inside the window (the usual case, and E stays inside): a
-                // block is accepted iff the energy after it is inside, i.e.
-                // lo - E <= Pk - R <= hi - E with R the sum of the blocks
-                // rejected so far.  Keep the bounds rlo = lo - E + R,
-                // rhi = hi - E + R; a rejection at j adds its block sum bj.
-                long long rlo = lo - E, rhi = hi - E;
-                while (rem) {
-                    const bool mine = (rem >> lane) & 1u;
-                    const bool viol = mine && (Pk < rlo || Pk > rhi);
-                    const unsigned vm = __ballot_sync(kFull, viol);
-                    if (vm == 0u) {
-                        acc |= rem;
-                        break;
-                    }
-                    const int j = __ffs(vm) - 1;
-                    acc |= rem & ((1u << j) - 1u);
-                    const long long bj = __shfl_sync(kFull, bk, j);
-                    rlo += bj;
-                    rhi += bj;
-                    rem &= ~((2u << j) - 1u);
-                }
-                // E after the group = E + P_last - R = lo + P_last - rlo
-                E = lo + __shfl_sync(kFull, Pk, 31 - __clz(em)) - rlo;
-            } else {
-                // General rule (outside the window): accept iff
-                // dist(E + dE_block) <= dist(E).
-                long long base = 0;
-                while (rem) {
-                    const long long Ea = E + (Pk - base);
-                    const long long Eb = Ea - bk;
-                    const bool mine = (rem >> lane) & 1u;
-                    const bool viol = mine && (dist_fx(Ea, lo, hi) > dist_fx(Eb, lo, hi));
-                    const unsigned vm = __ballot_sync(kFull, viol);
-                    if (vm == 0u) {
-                        const int last = 31 - __clz(rem);
-                        E += __shfl_sync(kFull, Pk, last) - base;
-                        acc |= rem;
-                        rem = 0u;
-                    } else {
-                        const int j = __ffs(vm) - 1;
-                        acc |= rem & ((1u << j) - 1u);
-                        const long long Pj = __shfl_sync(kFull, Pk, j);
-                        const long long bj = __shfl_sync(kFull, bk, j);
-                        E += (Pj - bj) - base;   // energy before the rejected block
-                        base = Pj;               // skip its contribution
-                        rem &= ~((2u << j) - 1u);
-                    }
-                }
-            }
+            const unsigned acc =
+                window_scan_group<false>(stg.P[g * 32 + lane], stg.endmask[g], B, E, lo, hi);
             if (lane == 0) stg.accmask[g] = acc;
         }
         bar_arrive(5 + s, NT);
@@ -630,12 +769,14 @@ __device__ __noinline__ void consume_class_muca(Smem<NWP> &sm, int nchunk, int m
 // One pass over the selected classes (mu = 0..3, parity 0,1).  Heat-bath:
 // class by class over the whole lattice.  Overrelaxation: slab by slab of the
 // last coordinate (x3 = t, the h range [t S, (t+1) S) of every class array,
-// S = L^3 / 2) and the classes within each slab.
+// S = L^3 / 2) and the classes within each slab, each group under the window
+// rule of the running energy (windowed false: no window, every reflection
+// is taken -- the multicanonical run).
 template <int NWP, bool FAST>
 __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t tag, int B,
-                         int class_mask, const KernelArgs *muca = nullptr)
+                         int class_mask, const KernelArgs *muca = nullptr, bool windowed = true)
 {
-    constexpr int CH = NWP * 32;
+    constexpr int NT = (NWP + 1) * 32, CH = NWP * 32;
     if (threadIdx.x == 0) sm.acc_cnt = 0ull;
     __syncthreads();
     const int half = sm.st.half, L = sm.st.L;
@@ -643,21 +784,52 @@ __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t
         // Overrelaxation: slab by slab (x3), all classes within a slab, so the
         // neighbours a slab's staples read are still in L2 from the class before.
         const int S = half / L;
+        const long long lo = windowed ? sm.st.lo_fx : -(1ll << 62);
+        const long long hi = windowed ? sm.st.hi_fx : (1ll << 62);
+        const long long bound = (long long)S * kOrDeltaMaxFx;
+        long long E = sm.st.E_fx;   // running energy, the same in every thread
+        int taken = 0;              // moves taken by this thread in decided groups
+        unsigned long long n_free = 0;
 #pragma unroll 1
         for (int t = 0; t < L; ++t) {
 #pragma unroll 1
             for (int cls = 0; cls < 8; ++cls) {
                 if (!((class_mask >> cls) & 1)) continue;
                 const int p = cls & 1;
-                switch (cls >> 1) {
-                    case 0: overrelax_class<0, NWP, FAST>(sm, th, p, t * S, S); break;
-                    case 1: overrelax_class<1, NWP, FAST>(sm, th, p, t * S, S); break;
-                    case 2: overrelax_class<2, NWP, FAST>(sm, th, p, t * S, S); break;
-                    default: overrelax_class<3, NWP, FAST>(sm, th, p, t * S, S); break;
+                // no decision of this group can depend on its moves' dE if E
+                // moves by less than `bound` and stays on one side of each edge
+                const bool free_group =
+                    (E - bound >= lo && E + bound <= hi) || E + bound < lo || E - bound > hi;
+                if (free_group) {
+                    switch (cls >> 1) {
+                        case 0: overrelax_class<0, NWP, FAST>(sm, th, p, t * S, S); break;
+                        case 1: overrelax_class<1, NWP, FAST>(sm, th, p, t * S, S); break;
+                        case 2: overrelax_class<2, NWP, FAST>(sm, th, p, t * S, S); break;
+                        default: overrelax_class<3, NWP, FAST>(sm, th, p, t * S, S); break;
+                    }
+                    n_free += (unsigned long long)S;
+                    __syncthreads();   // the next group reads the angles written here
+                } else {
+                    if (threadIdx.x == 0) sm.or_E = E;
+                    switch (cls >> 1) {
+                        case 0: taken += overrelax_class_scan<0, NWP, FAST>(sm, th, p, t * S, S, B); break;
+                        case 1: taken += overrelax_class_scan<1, NWP, FAST>(sm, th, p, t * S, S, B); break;
+                        case 2: taken += overrelax_class_scan<2, NWP, FAST>(sm, th, p, t * S, S, B); break;
+                        default: taken += overrelax_class_scan<3, NWP, FAST>(sm, th, p, t * S, S, B); break;
+                    }
+                    __syncthreads();
+                    E = sm.or_E;
                 }
-                __syncthreads();   // the next group reads the angles written here
             }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) taken += __shfl_down_sync(kFull, taken, o);
+        if ((threadIdx.x & 31) == 0 && taken) atomicAdd(&sm.acc_cnt, (unsigned long long)taken);
+        if (threadIdx.x == 0) {
+            atomicAdd(&sm.acc_cnt, n_free);
+            sm.st.E_fx = E;
+        }
+        (void)NT;
     } else {
         // Heat-bath: one class at a time over the whole lattice, so the
         // producer/consumer pipeline drains once per class.
@@ -683,6 +855,7 @@ __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t
             __syncthreads();   // the next class reads the angles written here
         }
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned long long n =
             (unsigned long long)__popc(class_mask & 0xFF) * (unsigned long long)half;
@@ -690,11 +863,68 @@ __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t
             sm.st.hb_acc += sm.acc_cnt;
             sm.st.hb_tot += n;
         } else {
-            sm.st.or_acc += n;
+            sm.st.or_acc += sm.acc_cnt;
             sm.st.or_tot += n;
         }
     }
     __syncthreads();
+}
+
+// cos(x) for x = hi + lo (|hi| <= 4 pi, |lo| tiny), accurate to about one
+// ulp and without systematic error, for the fixed-point plaquette sums: a
+// per-plaquette bias of 1e-9 would add up to ~1e-3 over the 960000
+// plaquettes of an L = 20 lattice (the accurate sincosf showed a mean error of
+// that order there), shifting the measured <<dE>>.
+//   Reduction (Cody & Waite, "Software Manual for the Elementary Functions",
+//   1980): k = nearest integer to hi 2/pi and x - k pi/2 = rh + rl with pi/2
+//   split into P1 + P2 + P3 (P1, P2 of 20 significant bits, so k P1 and k P2
+//   are exact for |k| <= 8): rh = hi - k P1 is exact and rl = lo - k P2 - k P3
+//   is tiny.  Rounding x - k P2 to one float instead would repeat the same
+//   rounding error for every angle of a binade (hi - k P1 lies on the float
+//   grid), a bias of ~2e-10 per plaquette.
+//   Evaluation: the Taylor series of cos and sin at rh in z = rh^2, truncated
+//   where the next term is below 1e-15; the coefficients 1/4!, 1/3! and 1/5!
+//   are carried as float pairs (their float rounding alone would bias the
+//   result by up to 5e-9); then cos(rh + rl) = cos rh - rl sin rh and
+//   sin(rh + rl) = sin rh + rl cos rh (plus the rl^2 terms), and
+//   cos x = cos r, -sin r, -cos r, sin r for k = 0, 1, 2, 3 (mod 4).
+__device__ __forceinline__ float cos_unbiased(float hi, float lo)
+{
+    const float k = rintf(hi * 0.636619747f);
+    const float rh = fmaf(-k, 1.5707950592041016f, hi);
+    float rl = fmaf(-k, 1.2675900507019833e-06f, lo);
+    rl = fmaf(-k, 7.4435477313145038e-13f, rl);
+    const float z = rh * rh;
+    // cos rh = 1 - z/2 + z^2/4! - ... - z^7/14!
+    float c = -1.147074536e-11f;
+    c = fmaf(c, z, 2.087675588e-09f);
+    c = fmaf(c, z, -2.755731998e-07f);
+    c = fmaf(c, z, 2.480158764e-05f);
+    c = fmaf(c, z, -1.388888923e-03f);
+    c = fmaf(c, z, -1.241763470e-09f);   // 1/4! = 4.166666791e-02 - 1.241763470e-09
+    c += 4.166666791e-02f;
+    c = fmaf(c, z, -0.5f);
+    c = fmaf(c, z, 1.0f);
+    // sin rh = rh (1 - z/3! + z^2/5! - ... - z^7/15!)
+    float t = -7.647163610e-13f;
+    t = fmaf(t, z, 1.605904437e-10f);
+    t = fmaf(t, z, -2.505210794e-08f);
+    t = fmaf(t, z, 2.755731884e-06f);
+    t = fmaf(t, z, -1.984127011e-04f);
+    t = fmaf(t, z, -4.346172033e-10f);   // 1/5! = 8.333333768e-03 - 4.346172033e-10
+    t += 8.333333768e-03f;
+    t = fmaf(t, z, 4.967053879e-09f);    // 1/3! = 1.666666716e-01 - 4.967053879e-09
+    t -= 1.666666716e-01f;
+    t = rh * fmaf(t, z, 1.0f);
+    // cos(rh + rl), sin(rh + rl) to second order in rl (|rl| <= 1e-5: the
+    // dropped -rl^2/2 alone would bias cos by up to -5e-11); the small terms
+    // are summed first, so the correction is not rounded away
+    const float h = 0.5f * rl * rl;
+    const float cr = c - fmaf(t, rl, c * h);
+    const float sr = t + fmaf(c, rl, -t * h);
+    const int q = (int)k & 3;
+    const float v = (q & 1) ? sr : cr;
+    return (q == 1 || q == 2) ? -v : v;
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
@@ -705,7 +935,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 }
 
 // cos of the plaquette angle a + b - c - d of four float angles: the angle is
-// formed exactly as hi + lo, cos(hi + lo) = cos(hi) - sin(hi) lo.
+// formed exactly as hi + lo and its cosine taken by cos_unbiased.
 __device__ __forceinline__ float plaquette_cos(float a, float b, float c, float d)
 {
     float s1, e1, s2, e2, hi, e3;
@@ -713,9 +943,7 @@ __device__ __forceinline__ float plaquette_cos(float a, float b, float c, float 
     two_sum(c, d, s2, e2);
     two_sum(s1, -s2, hi, e3);
     const float lo = (e1 - e2) + e3;
-    float sn, cs;
-    sincosf(hi, &sn, &cs);
-    return cs - sn * lo;
+    return cos_unbiased(hi, lo);
 }
 
 // Fresh energy of the CTA's lattice in fixed point: sum over the 6 V
@@ -849,8 +1077,8 @@ __global__ void __launch_bounds__((NWP + 1) * 32, min_ctas<NWP>()) llr_kernel(Ke
         args.program == kProgSweeps || args.program == kProgRM || args.program == kProgMuca;
     const int per_lat = multi ? args.n_therm + args.n_meas : 1;
     const unsigned n_items = (unsigned)args.n_lat * (unsigned)per_lat;
-    unsigned *counter = args.sync;
-    unsigned *err = args.sync + 1;
+    unsigned *err = args.sync;
+    unsigned *counter = args.sync + 1;
     unsigned *done = args.sync + 2;
     if (tid == 0) sm.cw = NWP;   // the consumer warp of a heat-bath pass: the last
     __syncthreads();
@@ -864,9 +1092,16 @@ __global__ void __launch_bounds__((NWP + 1) * 32, min_ctas<NWP>()) llr_kernel(Ke
                 state = 1;
                 if (j > 0) {
                     // sweep j-1 of this lattice was dequeued earlier by a running
-                    // CTA; wait for it, but never longer than wait_limit_ns
+                    // CTA; wait for it, but never longer than wait_limit_ns.  Once
+                    // any wait has run out (the error word is set; it stays set
+                    // until the host reads it), an item that would wait skips at
+                    // once: the sweep before it may never come.
                     const unsigned long long t0 = global_ns();
                     while (ld_acquire(done + slot) < (unsigned)j) {
+                        if (ld_acquire(err) != 0u) {
+                            state = 2;
+                            break;
+                        }
                         if (global_ns() - t0 > args.wait_limit_ns) {
                             atomicOr(err, 1u);
                             state = 2;
@@ -942,6 +1177,8 @@ __global__ void __launch_bounds__((NWP + 1) * 32, min_ctas<NWP>()) llr_kernel(Ke
                 if (args.pass_kind == 2)   // multicanonical heat-bath pass at slope a0
                     run_pass<NWP, FAST>(sm, th, 2, (float)args.muca_a0, kTagSweep, 1,
                                         args.class_mask, &args);
+                else if (args.pass_kind == 3)   // the end of a composite sweep
+                    end_of_sweep<NWP>(sm, th, false);
                 else
                     run_pass<NWP, FAST>(sm, th, args.pass_kind, (float)sm.st.a, kTagSweep,
                                         args.block, args.class_mask);
@@ -953,7 +1190,7 @@ __global__ void __launch_bounds__((NWP + 1) * 32, min_ctas<NWP>()) llr_kernel(Ke
                 // E, so every weight of E takes them), resync, energy history
                 run_pass<NWP, FAST>(sm, th, 2, (float)args.muca_a0, kTagSweep, 1, 0xFF, &args);
                 for (int k = 0; k < args.n_or; ++k)
-                    run_pass<NWP, FAST>(sm, th, 1, 0.0f, kTagSweep, 1, 0xFF);
+                    run_pass<NWP, FAST>(sm, th, 1, 0.0f, kTagSweep, 1, 0xFF, nullptr, false);
                 end_of_sweep<NWP>(sm, th, false);
                 if (tid == 0 && args.e_hist)
                     args.e_hist[(size_t)j * (size_t)args.n_lat + (size_t)lat] =
@@ -1111,7 +1348,9 @@ cudaError_t launch_t(const KernelArgs &a, cudaStream_t s)
     if (items <= 0) return cudaSuccess;
     const long long cap = resident_ctas<NWP, FAST>();
     const int grid = (int)(items < cap ? items : cap);
-    cudaError_t e = cudaMemsetAsync(a.sync, 0, sizeof(unsigned) * (size_t)(2 + a.n_lat), s);
+    // the item counter and the done counters; the error word sync[0] is left
+    // alone (sticky until the host reads and clears it)
+    cudaError_t e = cudaMemsetAsync(a.sync + 1, 0, sizeof(unsigned) * (size_t)(1 + a.n_lat), s);
     if (e != cudaSuccess) return e;
     llr_kernel<NWP, FAST><<<grid, (NWP + 1) * 32, stage_bytes<NWP>(), s>>>(a);
     return cudaGetLastError();

@@ -17,7 +17,8 @@ enum Program : int {
     kProgRM = 1,        // the same, then the Robbins-Monro update of a
     kProgApproach = 2,  // approach sweeps until E lies in the window
     kProgResync = 3,    // fresh energy -> tracked energy
-    kProgPass = 4,      // one heat-bath (pass_kind 0) or overrelaxation (1) pass, no resync
+    kProgPass = 4,      // one heat-bath (pass_kind 0), overrelaxation (1) or multicanonical
+                        // heat-bath (2) pass, no resync; or (3) the end of a composite sweep
     kProgBegin = 5,     // plain form: take a from a_in, clear the measurement
     kProgFinish = 6,    // plain form: resync + optional measurement + sweep counter
     kProgUpdate = 7,    // plain form: Robbins-Monro update from the accumulated measurement
@@ -40,9 +41,10 @@ struct KernelArgs {
     int *approach_sweeps; // nullable
     int n_or;
     int block;            // window-accept block size B (power of two, <= 32)
-    int pass_kind;        // pass: 0 heat-bath, 1 overrelaxation
+    int pass_kind;        // pass: 0 heat-bath, 1 overrelaxation, 2 multicanonical, 3 end of sweep
     int class_mask;       // pass: bit c selects class c = 2 mu + parity
-    // work queue (device): [0] item counter, [1] error word, [2 ..] sweeps done per slot
+    // work queue (device): [0] error word (sticky across launches, cleared by
+    // the host when it reads it), [1] item counter, [2 ..] sweeps done per slot
     unsigned *sync;
     unsigned long long wait_limit_ns;   // bounded wait for a lattice's previous sweep
     // graph replays: the Robbins-Monro step number lives in device memory

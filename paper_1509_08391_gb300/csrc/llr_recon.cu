@@ -11,7 +11,6 @@
 // one CTA: a block-wide FP64 scan for ln rho, log-sum-exp reductions for the
 // observables, and a device-side grid scan + golden-section search for the
 // C_V peak.
-#include <mutex>
 #include <string>
 
 #include "../../include/llr.h"
@@ -201,31 +200,18 @@ cudaError_t launch_cv_peak(int n, const double *c, const double *lr, double beta
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-double *g_noalloc_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device with that device current.
+// Device address of the scratch array in the current device's context,
+// looked up on every call (a cheap table lookup once the module is loaded):
+// a cached address would dangle after the context is destroyed and created
+// again (cudaDeviceReset, or the primary context released and retained).
 int noalloc_scratch(double **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess)
-        return llr::set_last_error(LLR_ERR_CUDA, (std::string("cudaGetDevice: ") +
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_lnrho);
+    if (e != cudaSuccess || !p)
+        return llr::set_last_error(LLR_ERR_CUDA, (std::string("cudaGetSymbolAddress: ") +
                                                   cudaGetErrorString(e)).c_str());
-    if (dev < 0 || dev >= kMaxDevices)
-        return llr::set_last_error(LLR_ERR_ARG, "device ordinal beyond 63");
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_lnrho);
-        if (e != cudaSuccess || !p)
-            return llr::set_last_error(LLR_ERR_CUDA, (std::string("cudaGetSymbolAddress: ") +
-                                                      cudaGetErrorString(e)).c_str());
-        g_noalloc_ptr[dev] = (double *)p;
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = (double *)p;
     return LLR_OK;
 }
 

@@ -46,3 +46,29 @@ def test_non_finite_slope_is_reported():
         with pytest.raises(llr.LLRError) as e:
             b.rm_step(np.array([np.nan, -1.0]), 1, 1, 0)
         assert e.value.code == llr.LLR_ERR_NUMERIC
+
+
+def test_one_timed_out_wait_does_not_stall_the_rest_of_the_launch():
+    """Once a bounded wait has run out, every later work item that would wait
+    skips at once instead of waiting out its own limit: 100000 sweeps of one
+    L = 16 lattice with a 5 ms limit (less than one sweep of one CTA) return
+    within about one sweep, where waiting out the limit item by item would
+    take ~(items / resident CTAs) x 5 ms, over a second."""
+    import time
+    full = workloads.uneven_batch()
+    w = workloads.subset(full, [next(i for i in range(full.n_lattices) if full.L[i] == 16)])
+    with llr.Batch.from_workload(w, max_approach=0) as b:
+        b.set_wait_limit(5_000_000)
+        t0 = time.perf_counter()
+        with pytest.raises(llr.LLRError) as e:
+            b.sweep(np.array([-1.0]), 100000)
+        dt = time.perf_counter() - t0
+        assert e.value.code == llr.LLR_ERR_TIMEOUT
+        assert dt < 0.4, dt
+        done = b.stats()["sweeps"][0]
+        assert 1 <= done < 100
+        # the error was read and cleared; the handle keeps working
+        b.set_wait_limit(20_000_000_000)
+        b.sweep(np.array([-1.0]), 2)
+        assert np.all(b.status() == 0)
+        assert b.stats()["sweeps"][0] == done + 2

@@ -7,7 +7,6 @@ import pytest
 
 import oracle
 from paper_1509_08391_gb300 import llr, workloads
-from tests.gpu_helpers import check_class_updates
 
 pytestmark = pytest.mark.gpu
 
@@ -22,26 +21,22 @@ def _built():
     oracle.build()
 
 
-def test_l20_class_updates_match_oracle_link_by_link():
-    """A window wide enough that no decision can flip makes every link of an
-    L=20 class update an independent output; each class of a heat-bath and of
-    an overrelaxation pass is checked from an identical state."""
-    full = workloads.l20_critical()
-    w = workloads.subset(full, [0, 1])
-    w.E_lo = [-1.0e7] * 2
-    w.dE = [2.0e7] * 2
-    with llr.Batch.from_workload(w, max_approach=0) as b:
-        b.set_kernel_config(BENCH_THREADS, BENCH_FAST)
-        b.sweep(np.full(2, -1.0), 2)         # leave the hot start
-        a = np.array([-1.011, -0.99])
-        worst, flips = check_class_updates(b, w, [1], a, classes=[0, 5])
-        assert flips == 0
-
-
 def test_l20_full_batch_properties():
     """The whole 2048-lattice batch: approach, one Robbins-Monro step of
-    1 + 2 sweeps; every energy stays in its window, tracked and FP64 energies
-    agree, acceptances are sane and nothing is NaN."""
+    1 + 2 sweeps, then one heat-bath and one overrelaxation pass.  Between
+    resyncs the running energy, which every window decision uses, never leaves
+    the window (it is checked after each pass, before any resync); at a
+    resync the fresh energy replaces it, and the two differ by the float32
+    rounding of the moves: the float32 staple sums carry ~1e-6 absolute error,
+    so a move changes the energy of the stored angles by ~1e-6 away from what
+    the running energy records (overrelaxation records nothing away from the
+    edges), a random walk bounded here by 5e-6 sqrt(updates since the last
+    resync) (3.2e6 link updates per composite sweep at L = 20).  The fresh
+    energy (int64 sum of the unbiased float32 plaquette cosines, ~2e-8 random
+    error each) matches the FP64 energy of the links within 2e-7 sqrt(6V)
+    (about 10 standard deviations); it is therefore inside the window up to the drift
+    bound, the measured <<dE>> lies in [-dE/2, dE/2] up to it, acceptances are
+    sane and nothing is NaN."""
     w = workloads.l20_critical()
     with llr.Batch.from_workload(w, max_approach=0) as b:
         b.set_kernel_config(BENCH_THREADS, BENCH_FAST)
@@ -51,15 +46,34 @@ def test_l20_full_batch_properties():
         b.stats(reset=True)
         a1, mean = b.rm_step(a, 1, 2, 0)
         assert np.all(np.isfinite(a1)) and np.all(b.status() == 0)
-        E = b.energy()
-        Et = b.tracked_energy()
         lo = np.asarray(w.E_lo)
         hi = lo + np.asarray(w.dE)
-        assert np.all(E >= lo - 0.05) and np.all(E <= hi + 0.05)
-        assert np.max(np.abs(E - Et)) < 1e-2
+        drift_bound = 5e-6 * np.sqrt(5 * 4 * 20 ** 4)
+        fresh_bound = 2e-7 * np.sqrt(6 * 20 ** 4)
+        E = b.energy()
+        Et = b.tracked_energy()     # the resync just set it to the fresh energy
+        print("\n[l20] fresh - FP64 energy: mean %.3g std %.3g max %.3g" %
+              ((Et - E).mean(), (Et - E).std(), np.abs(Et - E).max()))
+        assert np.all(E >= lo - drift_bound) and np.all(E <= hi + drift_bound)
+        assert np.max(np.abs(E - Et)) < fresh_bound
+        # no systematic error in the fresh energy beyond 1e-10 per plaquette
+        # (1e-4 at L = 20, a shift of a by 12 * 1e-4 / dE^2 < 1e-5; the
+        # library's accurate sincosf gave 4.6e-9 per plaquette)
+        assert abs((Et - E).mean()) < 1e-10 * 6 * 20 ** 4
         st = b.stats()
-        assert np.all(st["max_drift"] < 0.05)
+        print("\n[l20] max |tracked - fresh| at a resync: %.3g" % st["max_drift"].max())
+        assert np.all(st["max_drift"] < drift_bound)
         hb = st["hb_acc"].sum() / st["hb_tot"].sum()
         orr = st["or_acc"].sum() / st["or_tot"].sum()
         assert 0.5 < hb < 1.0 and orr > 0.99
-        assert np.all(np.abs(mean) <= 0.5 * np.asarray(w.dE) + 0.05)
+        assert np.all(np.abs(mean) <= 0.5 * np.asarray(w.dE) + drift_bound)
+        # the running energy after a heat-bath pass and after an
+        # overrelaxation pass (no resync in between): inside the window
+        for kind in (0, 1):
+            b.single_pass(kind, a1)
+            Et = b.tracked_energy()
+            inside = (Et >= lo) & (Et <= hi)
+            # a lattice whose resync left it just outside may still be
+            # returning (the rule only lets E approach the window)
+            outside_before = (E < lo) | (E > hi)
+            assert np.all(inside | outside_before), np.nonzero(~inside)[0][:5]

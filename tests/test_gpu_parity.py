@@ -1,8 +1,12 @@
-"""GPU path (CUDA library through the C ABI) against the FP64 oracle.
+"""GPU path (CUDA library through the C ABI) against the FP64 oracle at L = 4.
 
-Tolerances: link angles within 2e-5 rad (modulo 2 pi) after a few sweeps from
-an identical state; FP64 energies within 1e-9 relative on identical angles;
-Robbins-Monro slopes within the combined 3 sigma of the replica spreads.
+Tolerances (tests/gpu_helpers.py): every link of a class update within
+2e-5 rad + c 4e-6/|S| of the oracle from an identical state (c = 1 heat-bath,
+2 overrelaxation), every link of a whole overrelaxation pass within the same
+bound plus the propagated deviations of its earlier-updated neighbours;
+window decisions identical except near ties; FP64 energies within 1e-9
+relative on identical angles.  The full-size cases, the stepped trajectory
+and the Robbins-Monro statistics are in test_gpu_parity_fullsize.py.
 """
 import os
 
@@ -12,8 +16,8 @@ import pytest
 import oracle
 from oracle import recon
 from paper_1509_08391_gb300 import llr, workloads
-from tests.gpu_helpers import (TOL_RAD, check_class_updates, first_mismatch_class,
-                               oracle_mirror, wrapped_diff)
+from tests.gpu_helpers import check_class_updates, near_ties_are_rare, oracle_mirror
+from tests.test_gpu_parity_fullsize import _check_or_pass
 
 pytestmark = pytest.mark.gpu
 
@@ -97,8 +101,9 @@ def test_each_class_update_matches_oracle_link_by_link(block):
     a = np.linspace(-1.1, -0.9, w.n_lattices)
     with _batch(w, max_approach=1000) as b:
         b.sweep(a, 1)
-        worst, flips = check_class_updates(b, w, range(w.n_lattices), a)
-        assert worst < 1e-3 and flips <= 2
+        rep = check_class_updates(b, w, range(w.n_lattices), a)
+    assert rep["links"] == 2 * w.n_lattices * 1024 and rep["refused"] > 0
+    assert near_ties_are_rare(rep), rep
 
 
 def test_class_updates_match_oracle_at_zero_and_positive_slope():
@@ -108,61 +113,25 @@ def test_class_updates_match_oracle_at_zero_and_positive_slope():
     a = np.linspace(0.0, 1.2, w.n_lattices)
     with _batch(w, max_approach=1000) as b:
         b.sweep(np.full(w.n_lattices, -1.0), 1)
-        worst, flips = check_class_updates(b, w, range(w.n_lattices), a, kinds=(0,))
-        assert worst < 1e-3 and flips <= 2
-
-
-def test_heat_bath_trajectory_matches_oracle():
-    """Three heat-bath sweeps (n_or = 0) from one state: identical window
-    decisions and energies; links agree to 2e-5 rad except where float32
-    differences propagated through later classes of the same pass."""
-    w = workloads.small_l4()
-    w.n_or = 0
-    a = np.linspace(-1.1, -0.9, w.n_lattices)
-    with _batch(w, max_approach=1000) as b:
-        mirrors = [oracle_mirror(b, w, i) for i in range(w.n_lattices)]
-        b.stats(reset=True)
-        b.sweep(a, 3)
-        E = b.energy()
-        Et = b.tracked_energy()
-        st = b.stats()
-        for i, o in enumerate(mirrors):
-            hb0 = o.stats()["hb_acc"]
-            o.sweep(a[i], 3)
-            d = np.abs(wrapped_diff(b.get_links(i), o.links()))
-            assert np.mean(d < TOL_RAD) > 0.97 and d.max() < 1e-3, (i, d.max())
-            assert o.stats()["hb_acc"] - hb0 == st["hb_acc"][i]   # identical decisions
-            o2 = oracle_mirror(b, w, i)
-            assert abs(E[i] - o2.energy()) <= TOL_E_REL * abs(E[i])
-            # links differ by up to 1e-3 rad after propagation, so do the energies
-            assert abs(Et[i] - o.E) < 1e-2
-            assert w.E_lo[i] <= o.E <= w.E_lo[i] + w.dE[i]
+        rep = check_class_updates(b, w, range(w.n_lattices), a, kinds=(0,))
+    assert rep["links"] == w.n_lattices * 1024
+    assert near_ties_are_rare(rep), rep
 
 
 def test_full_overrelaxation_pass_matches_oracle_link_by_link():
-    """One whole overrelaxation pass (slab by slab of x3; in a slab the 8
-    classes mu = 0..3, parity 0, 1 in order) from an identical state: the
-    links agree within the float32 tolerance, except where float32
-    differences propagated through later links of the pass, and both sides
-    conserve the energy.  Any other order of the groups moves most links by
-    O(1)."""
+    """Two whole overrelaxation passes (slab by slab of x3; in a slab the 8
+    classes mu = 0..3, parity 0, 1 in order), each from the GPU's state: every
+    link within its tolerance, including the float32 deviations of the
+    neighbours updated before it in the same pass (any other order of the
+    groups moves links by O(1)); no refusals, and the running energies agree."""
     w = workloads.small_l4()
     a = np.full(w.n_lattices, -1.0)
+    rep = {}
     with _batch(w, max_approach=1000) as b:
         b.sweep(a, 1)
-        mirrors = [oracle_mirror(b, w, i) for i in range(w.n_lattices)]
-        E0 = b.energy()
-        b.single_pass(1, a)
-        E1 = b.energy()
-        for i, o in enumerate(mirrors):
-            S = o.staple_moduli()
-            o.single_pass(1, a[i])
-            d = np.abs(wrapped_diff(b.get_links(i), o.links()))
-            tol = TOL_RAD + 4e-6 / np.maximum(S, 1e-12)
-            # float32 differences grow through the later links of the pass
-            # (measured: ~92 % within tol, max ~4e-4); a wrong order is O(1)
-            assert np.mean(d <= tol) > 0.8 and d.max() < 5e-3, (i, float(d.max()))
-            assert abs(E1[i] - E0[i]) < 1e-2 and abs(o.energy() - E0[i]) < 1e-9 * abs(E0[i])
+        for _ in range(2):
+            _check_or_pass(b, w, a, rep)
+    assert rep["or_links"] == 2 * w.n_lattices * 1024
 
 
 def _oracle_composite_sweep(o, a, n_or, lo, hi):
@@ -241,31 +210,6 @@ def test_plain_form_equals_batched_form():
         assert np.array_equal(a1, a2) and np.array_equal(m1, m2)
         for i in range(w.n_lattices):
             assert np.array_equal(b1.get_links(i), b2.get_links(i))
-
-
-def test_robbins_monro_slopes_agree_with_oracle_statistically():
-    """8 intervals x 4 replicas at L=4, 10 RM steps of 10 + 40 sweeps on both sides:
-    the replica means agree within the combined 3 sigma (plus a floor for
-    intervals whose replicas happen to agree closely)."""
-    R = 4
-    w = workloads.small_l4(replicas=R)
-    n_rm, nth, nme = 10, 10, 40
-    a = np.full(w.n_lattices, w.a0)
-    with _batch(w, max_approach=1000) as b:
-        for n in range(n_rm):
-            a, _ = b.rm_step(a, nth, nme, n)
-        assert np.all(b.status() == 0)
-    g = oracle.Geom([4] * 4)
-    out = oracle.batch_run(g, w.seed, w.interval_id, w.replica_id, w.E_lo, w.dE,
-                           np.full(w.n_lattices, w.a0), n_or=w.n_or, block=w.block, n_therm=nth,
-                           n_meas=nme, n_rm=n_rm, max_approach=1000, beta_up=w.beta_up,
-                           beta_dn=w.beta_dn, n_threads=min(16, os.cpu_count() or 1))
-    ao = out["a"]
-    ga = a.reshape(8, R)
-    oa = ao.reshape(8, R)
-    sig = np.sqrt(ga.var(axis=1, ddof=1) / R + oa.var(axis=1, ddof=1) / R)
-    diff = np.abs(ga.mean(axis=1) - oa.mean(axis=1))
-    assert np.all(diff <= 3 * sig + 0.01), (diff, sig)
 
 
 def test_reconstruction_matches_oracle():
