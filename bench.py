@@ -803,8 +803,8 @@ def run_muca(args):
 def run_phases(args):
     """One launch per pass kind on 456 lattices of the benchmark workload (one
     full wave of 256-thread CTAs: 3 per SM on 152 SMs), so an ncu capture
-    (-k regex:llr_kernel) sees: resync, approach, overrelaxation pass,
-    heat-bath pass, composite sweep."""
+    (-k regex:llr_kernel) sees: resync, approach, two composite sweeps (one
+    launch), overrelaxation pass, heat-bath pass, composite sweep."""
     import torch
     torch.cuda.set_device(0)
     from paper_1509_08391_gb300 import build as bld
@@ -814,6 +814,7 @@ def run_phases(args):
     with llr.Batch.from_workload(w, max_approach=1000) as b:
         b.set_kernel_config(args.threads or 256, True)
         a = np.full(w.n_lattices, -1.01)
+        b.sweep(a, 2)           # leave the window edge the approach stops at
         b.single_pass(1, a)
         b.single_pass(0, a)
         b.sweep(a, 1)

@@ -65,7 +65,8 @@ constexpr int kStages = 4;
 // call t/2 (counter word 3), words 0-1 (t even) or 2-3 (t odd) as u1, u2,
 // and the lowest bit of the first of them as the sign of X:
 // z = cos(pi u1), f = (1 + r z) / (r + z), c = k (r - f); accept if
-// c (2 - c) > u2 or ln(c / u2) + 1 - c >= 0.  The accept test runs on fast
+// c (2 - c) > u2 or ln(c / u2) + 1 - c >= 0 (evaluated as
+// log2 c - log2 u2 >= (c - 1) / ln 2).  The accept test runs on fast
 // hardware approximations (it only decides which attempt is taken); the
 // accepted variate is then evaluated without cancellation as (cos X, sin X),
 // X = +-acos f: with sh, ch = sin, cos(pi u1 / 2) (hardware sine/cosine,
@@ -104,8 +105,9 @@ __device__ __forceinline__ bool von_mises(float kappa, uint32_t c0, uint32_t c1,
             const float z = __cosf(kPi * u1);
             const float f = __fdividef(1.0f + r * z, r + z);
             const float c = k * (rm1 + (1.0f - f));
-            if (!found &&
-                (c * (2.0f - c) - u2 > 0.0f || __logf(c) - __logf(u2) + 1.0f - c >= 0.0f)) {
+            // second test ln(c / u2) + 1 - c >= 0, in base 2
+            if (!found && (c * (2.0f - c) - u2 > 0.0f ||
+                           __log2f(c) - __log2f(u2) >= (c - 1.0f) * 1.4426950408889634f)) {
                 found = true;
                 w_acc = wa;
             }
@@ -270,8 +272,10 @@ struct Smem {
     LatState st;
     Stage<NWP> stage[kStages];
     long long red[NWP + 1];
-    // overrelaxation groups decided move by move: block-end / accept masks
-    // and the running energy
+    // overrelaxation groups decided move by move: per-warp sums of dE and
+    // |dE| (two buffers, one per chunk parity), block-end / accept masks and
+    // the running energy
+    int or_sum[2][NWP + 1], or_abs[2][NWP + 1];
     unsigned or_em[NWP + 1], or_acc[NWP + 1];
     long long or_E;
     unsigned long long acc_cnt;
@@ -592,31 +596,48 @@ __device__ __forceinline__ unsigned window_scan_group(long long Pk, unsigned em,
     return acc;
 }
 
-// One overrelaxation group whose running energy is within count * 2^-14 of a
-// window edge: the moves are decided in link order by the window rule on
-// their float32 dE estimates, which the running energy takes up.
-// Chunks of NT links: every thread forms its link's move and dE, the warps
-// form inclusive prefix sums; a chunk whose energy is at least NT * 2^-14 from
-// the edges is taken whole, otherwise warp 0 scans its 32-link groups in
-// order (window_scan_group) and the threads write the taken moves.  The
-// prefix sums are staged in the heat-bath's stage buffer (unused during an
-// overrelaxation pass).  The running energy enters and leaves in sm.or_E;
-// returns the number of moves this thread took.
+// One overrelaxation group whose running energy E is within count * 2^-14 of
+// a window edge, in chunks of NT links (one per thread), each in the cheapest
+// form that gives the window rule's decisions:
+//   * E farther than NT * 2^-14 from both edges: every move is taken, as in
+//     overrelax_class (no barrier, E unchanged);
+//   * otherwise every thread forms its link's move and float32 dE estimate;
+//     one barrier gives the chunk's sum of dE and of |dE| (per-warp
+//     reductions); if E +- sum|dE| stays clear of both edges (or entirely on
+//     one side outside), every move is taken and E takes up the sum;
+//   * only then are the moves decided in link order: warp prefix sums (staged
+//     in the heat-bath's stage buffer, unused during an overrelaxation pass),
+//     warp 0 scans the 32-link groups (window_scan_group), the threads write
+//     the taken moves and E takes up their dE.
+// Chunks of one group need no barrier between them: links of one class do
+// not interact.  E enters as an argument (the same in every thread) and
+// leaves in sm.or_E, which thread 0 has set to it before the call; returns
+// the number of moves this thread took.
 template <int MU, int NWP, bool FAST>
 __device__ __noinline__ int overrelax_class_scan(Smem<NWP> &sm, float *th, int p, int h0,
-                                                 int count, int B)
+                                                 int count, int B, long long E)
 {
     constexpr int NT = (NWP + 1) * 32;
     const int L = sm.st.L, half = sm.st.half;
     const uint32_t magic = sm.st.magic;
     const long long lo = sm.st.lo_fx, hi = sm.st.hi_fx;
+    const long long m = (long long)NT * kOrDeltaMaxFx;
     float *own = th + (2 * MU + p) * half;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     long long *stP = reinterpret_cast<long long *>(g_stage_buf);
-    int taken = 0;
+    int taken = 0, par = 0;
     for (int c0 = 0; c0 < count; c0 += NT) {
         const int local = c0 + tid;
         const bool valid = local < count;
+        if ((E - m >= lo && E + m <= hi) || E + m < lo || E - m > hi) {
+            if (valid) {
+                int dfx;
+                own[h0 + local] =
+                    overrelax_link<MU, FAST, false>(th, own, half, L, magic, p, h0 + local, dfx);
+                ++taken;
+            }
+            continue;
+        }
         int dfx = 0;
         float tn = 0.0f;
         bool ok = false;
@@ -624,6 +645,29 @@ __device__ __noinline__ int overrelax_class_scan(Smem<NWP> &sm, float *th, int p
             tn = overrelax_link<MU, FAST, true>(th, own, half, L, magic, p, h0 + local, dfx);
             ok = dfx != kOrRefused;
             if (!ok) dfx = 0;
+        }
+        // |dfx| <= 2^18, so a warp's sums fit in 32 bits
+        const int ws = __reduce_add_sync(kFull, dfx);
+        const int wa = __reduce_add_sync(kFull, dfx < 0 ? -dfx : dfx);
+        if (lane == 0) {
+            sm.or_sum[par][warp] = ws;
+            sm.or_abs[par][warp] = wa;
+        }
+        __syncthreads();
+        long long cs = 0, ca = 0;
+#pragma unroll
+        for (int w = 0; w <= NWP; ++w) {
+            cs += sm.or_sum[par][w];
+            ca += sm.or_abs[par][w];
+        }
+        par ^= 1;
+        if ((E - ca >= lo && E + ca <= hi) || E + ca < lo || E - ca > hi) {
+            if (valid && ok) {
+                own[h0 + local] = tn;
+                ++taken;
+            }
+            E += cs;
+            continue;
         }
         long long P = dfx;
 #pragma unroll
@@ -637,22 +681,13 @@ __device__ __noinline__ int overrelax_class_scan(Smem<NWP> &sm, float *th, int p
         if (lane == 0) sm.or_em[warp] = em;
         __syncthreads();
         if (warp == 0) {
-            long long E = sm.or_E;
-            const long long m = (long long)NT * kOrDeltaMaxFx;
-            const bool whole = (E - m >= lo && E + m <= hi) || E + m < lo || E - m > hi;
+            long long Ew = E;
             for (int g = 0; g <= NWP; ++g) {
-                const unsigned emg = sm.or_em[g];
-                const long long Pg = stP[g * 32 + lane];
-                unsigned acc;
-                if (whole) {
-                    acc = emg;
-                    if (emg) E += __shfl_sync(kFull, Pg, 31 - __clz(emg));
-                } else {
-                    acc = window_scan_group<true>(Pg, emg, B, E, lo, hi);
-                }
+                const unsigned acc = window_scan_group<true>(stP[g * 32 + lane], sm.or_em[g], B,
+                                                             Ew, lo, hi);
                 if (lane == 0) sm.or_acc[g] = acc;
             }
-            if (lane == 0) sm.or_E = E;
+            if (lane == 0) sm.or_E = Ew;
         }
         __syncthreads();
         if (valid && ok) {
@@ -662,7 +697,9 @@ __device__ __noinline__ int overrelax_class_scan(Smem<NWP> &sm, float *th, int p
                 ++taken;
             }
         }
+        E = sm.or_E;
     }
+    if (threadIdx.x == 0) sm.or_E = E;
     return taken;
 }
 
@@ -812,10 +849,10 @@ __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t
                 } else {
                     if (threadIdx.x == 0) sm.or_E = E;
                     switch (cls >> 1) {
-                        case 0: taken += overrelax_class_scan<0, NWP, FAST>(sm, th, p, t * S, S, B); break;
-                        case 1: taken += overrelax_class_scan<1, NWP, FAST>(sm, th, p, t * S, S, B); break;
-                        case 2: taken += overrelax_class_scan<2, NWP, FAST>(sm, th, p, t * S, S, B); break;
-                        default: taken += overrelax_class_scan<3, NWP, FAST>(sm, th, p, t * S, S, B); break;
+                        case 0: taken += overrelax_class_scan<0, NWP, FAST>(sm, th, p, t * S, S, B, E); break;
+                        case 1: taken += overrelax_class_scan<1, NWP, FAST>(sm, th, p, t * S, S, B, E); break;
+                        case 2: taken += overrelax_class_scan<2, NWP, FAST>(sm, th, p, t * S, S, B, E); break;
+                        default: taken += overrelax_class_scan<3, NWP, FAST>(sm, th, p, t * S, S, B, E); break;
                     }
                     __syncthreads();
                     E = sm.or_E;

@@ -37,10 +37,13 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
     return U4{c0, c1, c2, c3};
 }
 
-// Uniform in the open interval (0,1): (2 * (w >> 9) + 1) * 2^-24, exact in float.
+// Uniform in the open interval (0,1): (2 * (w >> 9) + 1) * 2^-24, exact in float,
+// formed without an integer-to-float conversion: the float 1.m with the top 23
+// bits of w as mantissa is 1 + (w >> 9) 2^-23, and subtracting 1 - 2^-24 (exact:
+// the difference is representable) leaves (2 (w >> 9) + 1) 2^-24.
 __device__ __forceinline__ float u01(uint32_t w)
 {
-    return (float)((w >> 9) * 2u + 1u) * 5.9604644775390625e-8f;
+    return __uint_as_float(0x3F800000u | (w >> 9)) - 0.99999994039535522f;
 }
 
 constexpr float kPi = 3.14159265358979323846f;
