@@ -4,8 +4,8 @@
  *
  * Paper: K. Langfeld, B. Lucini, R. Pellegrini, A. Rago, "An efficient
  * algorithm for numerical computations of continuous densities of states",
- * arXiv:1509.08391.  Equations are cited by the labels of the paper's source
- * (eq. kk21 = the under-relaxed Robbins-Monro update of Sec. 2.2).
+ * arXiv:1509.08391.  Equations are cited by their printed numbers
+ * (eq. (2.30) = the under-relaxed Robbins-Monro update of Sec. 2.2).
  *
  * Conventions shared by every entry point
  *   - Return value: 0 on success, a negative LLR_ERR_* code on failure;
@@ -18,9 +18,9 @@
  *     lattice energies, windows and counters) until llr_destroy.  Calls on
  *     one handle are not thread safe; they are ordered on the stream given to
  *     llr_init_lattice (NULL = the legacy default stream).
- *   - The slope convention follows eq. kk1a: a = d ln rho / dE, and the
+ *   - The slope convention follows eq. (2.4): a = d ln rho / dE, and the
  *     restricted ensemble has weight exp(-a E) on the closed window
- *     E_lo <= E <= E_lo + dE (eqs. kk7-kk8).  In the physical range a < 0
+ *     E_lo <= E <= E_lo + dE (eqs. (2.13)-(2.14)).  In the physical range a < 0
  *     and the canonical coupling is beta = -a.
  *   - Link angles are float32 in [-pi, pi); E = sum over plaquettes of
  *     cos(theta_P) (Sec. 3.1, beta factored out).  The canonical host layout
@@ -89,9 +89,9 @@ int llr_approach(llr_handle h, int max_sweeps, int *sweeps_out);
  * from the closed window; an overrelaxation block (a reflection, which keeps
  * E in exact arithmetic) is taken iff E + dE lies in the window or E does
  * not, and a reflection with |dE| > 2^-14 is refused.  Inside the window both
- * are the indicator of eq. kk7.
+ * are the indicator of eq. (2.13).
  * If measure != 0, dE_sum_out (host double[n_lattices], nullable) receives
- * the sum over these sweeps of E - E_lo - dE/2 (eq. kk10).  Synchronous. */
+ * the sum over these sweeps of E - E_lo - dE/2 (eq. (2.16)).  Synchronous. */
 int llr_sweep(llr_handle h, const double *a, int n_sweeps, int measure, double *dE_sum_out);
 
 /* One pass of a composite sweep for every lattice, without the energy
@@ -108,7 +108,7 @@ int llr_sweep(llr_handle h, const double *a, int n_sweeps, int measure, double *
  * bit.  Synchronous. */
 int llr_pass(llr_handle h, int kind, const double *a, int class_mask);
 
-/* One Robbins-Monro iteration for every lattice (Algorithm 1, eq. kk21):
+/* One Robbins-Monro iteration for every lattice (Algorithm 1, eq. (2.30)):
  * n_therm + n_meas composite sweeps at a, <<dE>> = mean over the last n_meas
  * sweeps of E - E_lo - dE/2, then a <- a + 12 <<dE>> / (dE^2 (rm_index + 1)).
  * a_inout: host double[n_lattices]; dE_mean_out: host double[n_lattices] or
@@ -128,7 +128,7 @@ int llr_rm_step_dev(llr_handle h, int n_therm, int n_meas, int rm_index, const d
 /* n_steps Robbins-Monro iterations (Algorithm 1's loop over n) of every
  * lattice, as replays of one captured CUDA graph (reset of the work queue,
  * the persistent kernel, and an increment of a device step counter): step k
- * uses rm_index0 + k in eq. kk21.  a_dev: device double[n_lattices], a^(n)
+ * uses rm_index0 + k in eq. (2.30).  a_dev: device double[n_lattices], a^(n)
  * in, a^(n + n_steps) out; hist_dev: device double[n_steps][n_lattices] of
  * a after each step, or NULL.  Asynchronous on the handle's stream.  The
  * graph is captured on the first call and reused while the arguments stay
@@ -145,11 +145,11 @@ int llr_rm_run(llr_handle h, int n_therm, int n_meas, int rm_index0, int n_steps
 int llr_rm_step_plain(llr_handle h, int n_therm, int n_meas, int rm_index, double *a_inout,
                       double *dE_mean_out);
 
-/* Weight of the multicanonical run (Sec. 2.6, eq. 4.1): W(E) = 1/rho~(E),
- * with ln rho~ the piecewise-linear density of eq. rhoguess on n contiguous
+/* Weight of the multicanonical run (Sec. 2.6, eq. (2.50)): W(E) = 1/rho~(E),
+ * with ln rho~ the piecewise-linear density of eq. (2.10) on n contiguous
  * intervals of width de starting at e0 (ln rho~ = 0 at e0, slope a[k] inside
  * interval k) and continued beyond the first / last interval with their
- * slopes (the tails of eq. 4.1 at the micro-canonical beta_1, beta_2).
+ * slopes (the tails of eq. (2.50) at the micro-canonical beta_1, beta_2).
  * a0 is the slope of the heat-bath proposals (any value; Metropolis-Hastings
  * corrects it, and a0 near the slopes keeps the acceptance high).  a: host
  * double[n].  Copied to the device; applies to every lattice of the handle.
@@ -218,12 +218,12 @@ int llr_stats(llr_handle h, double *out, int reset);
 int llr_status(llr_handle h, int *out);
 
 /* Reconstruction of ln rho at the interval centres by the trapezium rule
- * (eqs. kk3a, kk3b): ln_rho[0] = 0, ln_rho[k+1] = ln_rho[k] + (c[k+1] - c[k])
+ * (eqs. (2.6), (2.7)): ln_rho[0] = 0, ln_rho[k+1] = ln_rho[k] + (c[k+1] - c[k])
  * (a[k] + a[k+1]) / 2.  centres (ascending), a, ln_rho_out: host double[n].
  * Computed in FP64 on the device. */
 int llr_reconstruct_lnrho(int n, const double *centres, const double *a, double *ln_rho_out);
 
-/* Action observables from the reconstructed density (eqs. l19, l20) at each
+/* Action observables from the reconstructed density (eqs. (2.46), (2.47)) at each
  * of n_beta couplings: ln Z, <E>, <E^2>, in FP64 log-space on the device.
  * Centres must be equally spaced (weight = spacing).  All host arrays. */
 int llr_observables(int n, const double *centres, const double *a, int n_beta,
@@ -272,14 +272,33 @@ int llr_cv_peak(int n, const double *centres, const double *a, double beta_lo, d
  * Chosen per lattice size by the autotuner; default 256 threads, fast math. */
 int llr_set_kernel_config(llr_handle h, int threads, int fast_math);
 
+/* The full launch shape of the batched sweep kernel, as the autotuner sets
+ * it; none of these changes the chains (every shape runs the same per-link
+ * arithmetic in the same order), only the speed.
+ *   threads, fast_math: as llr_set_kernel_config.
+ *   ring: stages of the heat-bath producer/consumer ring in use, 1, 2 or 4
+ *     (how many 32-link-group chunks the proposing warps may run ahead of
+ *     the warp that takes the window decisions).
+ *   carveout: preferred share of the SM's unified L1/shared storage given to
+ *     shared memory, in percent: 50, 75 or 100, or -1 for the driver's default
+ *     (a hint; it is a property of the kernel variant in this process, so the
+ *     last value set for a variant applies to every handle launching it).
+ * Errors: LLR_ERR_ARG for any other value. */
+int llr_set_kernel_shape(llr_handle h, int threads, int fast_math, int ring, int carveout);
+
+/* The shape of the last launch of the batched sweep kernel on this handle:
+ * out (host int[5]) = {threads per CTA, fast math, ring stages, carve-out,
+ * CTAs launched}; all zero before the first launch. */
+int llr_get_last_launch(llr_handle h, int *out);
+
 /* ---------------------------------------------------------------------------
  * Learned warm start of the Robbins-Monro iteration (no counterpart in the
  * paper's algorithm; the paper's justification is that a_k is an intrinsic,
- * volume independent quantity, Sec. 2.2 eq. kk2 and the appendix eqs.
- * kkk34-kkk36, and that the initial a only needs to be close, Sec. 2.4).
+ * volume independent quantity, Sec. 2.2 eq. (2.5) and the appendix eqs.
+ * (A.11)-(A.13), and that the initial a only needs to be close, Sec. 2.4).
  * A multilayer perceptron 3 -> 64 -> 64 -> 64 -> 1 with GELU (erf form)
  * maps the standardised features (1/V, E/6V, dE/6V), V = L^4 (finite-volume
- * corrections of a_k are O(1/V), eq. kkk35), to a; FP32 parameters
+ * corrections of a_k are O(1/V), eq. (A.12)), to a; FP32 parameters
  * in one array: W1 (3x64, [in][out]), b1, W2 (64x64), b2, W3 (64x64), b3,
  * W4 (64x1), b4 (llr_mlp_num_params() floats).  Loss: mean squared error.
  * All input arrays are host double[n]; calls are synchronous on the stream

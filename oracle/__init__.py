@@ -273,9 +273,9 @@ class Lattice:
 
 
 class MucaWeight:
-    """ln rho~ of eq. rhoguess from the slopes of n contiguous intervals of width
+    """ln rho~ of eq. (2.10) from the slopes of n contiguous intervals of width
     de starting at e0, continued linearly beyond them: the weight 1/rho~ of the
-    multicanonical run (Sec. 2.6, eq. 4.1)."""
+    multicanonical run (Sec. 2.6, eq. (2.50))."""
 
     def __init__(self, e0, de, a):
         a = np.ascontiguousarray(a, dtype=np.float64)

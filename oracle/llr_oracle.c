@@ -9,20 +9,19 @@
  *
  * Paper: K. Langfeld, B. Lucini, R. Pellegrini, A. Rago, "An efficient
  * algorithm for numerical computations of continuous densities of states"
- * (arXiv:1509.08391).  Equations are cited by the labels of the paper's
- * source, e.g. "eq. kk21" is the under-relaxed Robbins-Monro update of
- * Sec. 2.2.
+ * (arXiv:1509.08391).  Equations are cited by their printed numbers, e.g.
+ * eq. (2.30) is the under-relaxed Robbins-Monro update of Sec. 2.2.
  *
  * What is computed (and where it is defined):
  *   - Sec. 3.1: link angles theta_mu(x) in [-pi,pi), plaquette angle
  *     theta_munu(x) = theta_mu(x) + theta_nu(x+mu) - theta_mu(x+nu) - theta_nu(x),
  *     energy E = sum_{x, mu<nu} cos theta_munu(x) (beta factored out), Haar
  *     measure prod dtheta/2pi.
- *   - Sec. 2.2, eqs. kk7-kk10: expectation values restricted to the closed
+ *   - Sec. 2.2, eqs. (2.13)-(2.16): expectation values restricted to the closed
  *     window E_k <= E <= E_k + dE, reweighted by exp(-a E).
  *   - Sec. 2.4, Algorithm 1: N_TH + N_SW importance-sampling sweeps per
  *     Robbins-Monro iteration, measuring E after N_TH, then the update of a.
- *   - Sec. 2.2, eq. kk21: a <- a + 12 <<dE>> / (dE^2 (n+1)) (sign of kk21;
+ *   - Sec. 2.2, eq. (2.30): a <- a + 12 <<dE>> / (dE^2 (n+1)) (sign of eq. (2.30);
  *     Algorithm 1 prints the opposite sign, see the readings below).
  *
  * Readings where the paper is silent:
@@ -45,14 +44,16 @@
  *      the restricted measure: a heat-bath block is
  *      accepted iff dist(E + dE_block) <= dist(E), where dist is the distance
  *      of E from the window (0 inside).  Inside the window this is exactly
- *      the indicator of eq. kk7; outside it only lets E move towards the
+ *      the indicator of eq. (2.13); outside it only lets E move towards the
  *      window (used while approaching the window from a hot start).
- *  R19 overrelaxation blocks: the reflection keeps E in exact arithmetic, so a
- *      block is accepted iff E + dE_block lies in the window, or E does not
- *      (outside the window reflections are always taken; in FP64 the dE of a
- *      reflection, ~1e-15, is below the resolution of E and the dist rule
- *      would take them too).  A reflection whose |dE| exceeds 2^-14 is
- *      refused (a guard for float32 arithmetic; FP64 never reaches it).
+ *  R19 overrelaxation blocks: the reflection keeps E in exact arithmetic, so
+ *      the running energy is not moved by overrelaxation moves (their dE is
+ *      rounding, ~1e-15 in FP64) and a block is accepted iff E + dE_block lies
+ *      in the window, or E does not (outside the window reflections are
+ *      always taken), E being the running energy before the pass.  A
+ *      reflection whose |dE| exceeds 2^-14 is refused (a guard for float32
+ *      arithmetic; FP64 never reaches it).  The fresh energy at the end of the
+ *      composite sweep takes up the moves' rounding.
  *   R3 heat-bath proposal: von Mises variate by Best & Fisher (1979).
  *   R4 random numbers: Philox4x32-10 (Salmon et al., SC'11), keyed by
  *      (seed, interval, replica), counter (link, sweep, tag, attempt / 2):
@@ -67,8 +68,8 @@
  *      intervals tried in one exchange round and a round number; the draw
  *      deciding a pair comes from Philox keyed by the pair's first lattice,
  *      counter (0, round, swap tag, 0), as a 53-bit uniform in [0, 1).
- *   R8 multicanonical run (Sec. 2.6, eq. 4.1): weight W(E) = 1/rho~(E), with
- *      ln rho~ the piecewise-linear function of eq. rhoguess built from the
+ *   R8 multicanonical run (Sec. 2.6, eq. (2.50)): weight W(E) = 1/rho~(E), with
+ *      ln rho~ the piecewise-linear function of eq. (2.10) built from the
  *      slopes of n contiguous intervals and continued linearly with the end
  *      slopes outside them (the micro-canonical beta_1, beta_2 tails).  A
  *      heat-bath pass proposes every link of a class from its conditional
@@ -459,10 +460,11 @@ static double dist_to_window(double E, double lo, double hi)
 }
 
 /* The window decision of one block of a group (R2, R19).  Heat-bath (mode
- * 0): taken iff dist(E + d) <= dist(E).  Overrelaxation (mode 1): the
- * reflection keeps E in exact arithmetic, so outside the window it is always
- * taken and inside it is taken iff E + d stays inside.  Inside the window
- * both are the indicator of eq. kk7. */
+ * 0): taken iff dist(E + d) <= dist(E), E the running energy.  Overrelaxation
+ * (mode 1): the reflection keeps E in exact arithmetic, so outside the window
+ * it is always taken and inside it is taken iff E + d stays inside, E being
+ * the energy before the pass (overrelaxation does not move the running
+ * energy).  Inside the window both are the indicator of eq. (2.13). */
 static int block_taken(int mode, double E, double d, double lo, double hi)
 {
     if (mode == 1) return dist_to_window(E, lo, hi) > 0.0 || dist_to_window(E + d, lo, hi) == 0.0;
@@ -524,7 +526,7 @@ static void group_update(orc_lat *t, int c0, int c1, int mode, double a, uint32_
         int acc = block_taken(mode, t->E, d, lo, hi);
         if (acc) {
             for (int i = b0; i < b1; ++i) t->theta[g->class_links[i]] = t->prop[g->class_links[i]];
-            t->E += d;
+            if (mode == 0) t->E += d;   /* R19: overrelaxation leaves the running energy */
         }
         if (mode == 0) { t->hb_tot += b1 - b0; if (acc) t->hb_acc += b1 - b0; }
         else           { t->or_tot += b1 - b0; if (acc) t->or_acc += b1 - b0; }
@@ -582,7 +584,7 @@ int orc_lat_class_trace(orc_lat *t, int cls, int mode, double a, double *th_old,
                 dE_block[i - c0] = d;
                 accepted[i - c0] = acc;
             }
-            if (acc) E += d;
+            if (acc && mode == 0) E += d;
         }
     }
     return c1 - c0;
@@ -651,7 +653,7 @@ int orc_lat_approach(orc_lat *t, int max_sweeps)
     return s;
 }
 
-/* One Robbins-Monro iteration (Algorithm 1 inner loop, eq. kk21):
+/* One Robbins-Monro iteration (Algorithm 1 inner loop, eq. (2.30)):
  * n_therm + n_meas composite sweeps at weight exp(-a E); the mean of
  * E - E_lo - dE/2 over the last n_meas sweeps gives <<dE>>; then
  * a <- a + 12 <<dE>> / (dE^2 (rm_index + 1)).  Returns the new a. */
@@ -707,9 +709,9 @@ int orc_replica_exchange(orc_lat **lats, int n_pairs, const int *pairs, const do
 }
 
 /* ------------------------------------------------------------------------
- * Multicanonical update (Sec. 2.6, eq. 4.1).  ln rho~ at the edges of n
+ * Multicanonical update (Sec. 2.6, eq. (2.50)).  ln rho~ at the edges of n
  * contiguous intervals of width de from e0: lnr[0] = 0,
- * lnr[k+1] = lnr[k] + a_k de (eq. rhoguess), linear with slope a_k inside
+ * lnr[k+1] = lnr[k] + a_k de (eq. (2.10)), linear with slope a_k inside
  * interval k and with the first / last slope beyond the ends.
  * ---------------------------------------------------------------------- */
 typedef struct {

@@ -4,14 +4,14 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 The paper has no network; this is the learned warm start of the Robbins-
 Monro iteration.  The paper's reason it can work: the slopes a_k are
-intrinsic (volume independent) quantities, Sec. 2.2 eq. kk2 and the
-appendix, eqs. kkk34-kkk36, so a map (L, E/6V, dE) -> a learned on small
+intrinsic (volume independent) quantities, Sec. 2.2 eq. (2.5) and the
+appendix, eqs. (A.11)-(A.13), so a map (L, E/6V, dE) -> a learned on small
 volumes predicts larger ones; Sec. 2.4 says a good initial a only needs to be
 close to the result.
 
 Definition (both the oracle and the CUDA kernels implement exactly this):
   features  x = ((1/V, E/6V, dE/6V) - mean) / std   (V = L^4; training-set statistics;
-            1/V because the finite-volume corrections of a_k are O(1/V), eq. kkk35)
+            1/V because the finite-volume corrections of a_k are O(1/V), eq. (A.12))
   h1 = gelu(x W1 + b1)      W1: 3x64
   h2 = gelu(h1 W2 + b2)     W2: 64x64
   h3 = gelu(h2 W3 + b3)     W3: 64x64

@@ -5,12 +5,12 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 Follows Sec. 2.2 and Sec. 2.3 of Langfeld, Lucini, Pellegrini, Rago
 (arXiv:1509.08391):
 
-* eq. kk3a / kk3b: the trapezium rule on the slopes a_k gives
+* eq. (2.6) / (2.7): the trapezium rule on the slopes a_k gives
   ln rho at consecutive interval centres,
   ln rho(c_{k+1}) - ln rho(c_k) = (c_{k+1} - c_k) (a_k + a_{k+1}) / 2,
   fixed up to an additive constant by ln rho(c_0) = 0.  For contiguous
   intervals c_{k+1} - c_k = dE, which is the paper's form.
-* eq. l19 / l20: action observables as sums over the centres,
+* eq. (2.46) / (2.47): action observables as sums over the centres,
   Z(beta) = sum_k w exp(ln rho(c_k) + beta c_k) and
   <E^m> = sum_k w c_k^m exp(ln rho(c_k) + beta c_k) / Z, with w the spacing
   of the (uniformly spaced) centres.
@@ -34,7 +34,7 @@ def lnrho_at_centres(c, a):
 
 
 def moments(c, a, beta):
-    """(ln Z, <E>, <E^2>) at one beta from eqs. l19-l20."""
+    """(ln Z, <E>, <E^2>) at one beta from eqs. (2.46)-(2.47)."""
     c = np.asarray(c, dtype=np.float64)
     w = (c[-1] - c[0]) / (len(c) - 1) if len(c) > 1 else 1.0
     x = lnrho_at_centres(c, a) + beta * c

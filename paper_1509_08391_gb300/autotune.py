@@ -1,11 +1,23 @@
 """Autotuner of the batched sweep kernel's launch shape.
 
-The CTA shapes (128, 160, 192, 256, 512 threads; one consumer warp, the rest
-producers) run identical per-link arithmetic, so the choice changes speed
-only, never results.  For a workload the tuner builds a scratch batch of the
-same lattices (the caller's chains are not advanced), times one composite
-sweep per shape with CUDA events after a warm-up sweep, and caches the
-fastest shape per (GPU, lattice sizes, batch size) in a JSON file.
+Knobs (none changes the chains: every shape runs the same per-link
+arithmetic in the same order, so the choice changes speed only):
+  * threads per CTA: 128, 160, 192, 256, 512 (one warp takes the window
+    decisions, the others propose; the chunk of a heat-bath pass is the
+    proposing warps x 32 links, so this also sets the chunk size);
+  * ring: stages of the producer/consumer ring in use (1, 2, 4), how many
+    chunks the proposing warps may run ahead of the deciding warp;
+  * carveout: the shared-memory share of the SM's unified L1/shared storage
+    (driver default, 50, 75 or 100 percent).
+The order of the overrelaxation groups (slab by slab of x3) is not a knob:
+it is part of the update order of the Markov chain (reading R1), so another
+grouping would be another chain.
+
+For a workload the tuner builds a scratch batch of the same lattices (the
+caller's chains are not advanced), times two composite sweeps per candidate
+with CUDA events after a warm-up sweep, searching one knob at a time (threads,
+then ring, then carve-out) from the defaults, and caches the fastest shape per
+(GPU, lattice sizes, batch size) in a JSON file.
 """
 from __future__ import annotations
 
@@ -18,6 +30,9 @@ from . import llr, workloads
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
 SHAPES = (128, 160, 192, 256, 512)
+RINGS = (1, 2, 4)
+CARVEOUTS = (-1, 50, 75, 100)
+DEFAULT = {"threads": 256, "ring": 4, "carveout": -1}
 
 
 def _key(w: workloads.Workload, gpu: str) -> str:
@@ -41,31 +56,48 @@ def _save(d):
     os.replace(tmp, CACHE)
 
 
-def tune(w: workloads.Workload, shapes=SHAPES, use_cache=True, verbose=False):
-    """Best threads-per-CTA for this workload (fast math on)."""
+def apply(batch: "llr.Batch", shape: dict, fast_math: bool = True):
+    batch.set_kernel_shape(shape["threads"], fast_math, shape["ring"], shape["carveout"])
+
+
+def tune(w: workloads.Workload, use_cache=True, verbose=False, sweeps=2):
+    """Fastest launch shape {threads, ring, carveout} for this workload (fast
+    math on); the per-candidate times are kept in the cache entry."""
     import torch
     gpu = torch.cuda.get_device_name()
     key = _key(w, gpu)
     cache = _load()
-    if use_cache and key in cache:
-        return int(cache[key]["threads"])
+    if use_cache and key in cache and "shape" in cache[key]:
+        return dict(cache[key]["shape"])
     times = {}
     stream = torch.cuda.Stream()
-    with llr.Batch.from_workload(w, stream=stream.cuda_stream, max_approach=1000) as b:
+    best = dict(DEFAULT)
+    with llr.Batch.from_workload(w, stream=stream.cuda_stream, max_approach=5000) as b:
         a = np.full(w.n_lattices, w.a0)
-        for t in shapes:
-            b.set_kernel_config(t, True)
+
+        def run(shape):
+            name = "t%d_r%d_c%d" % (shape["threads"], shape["ring"], shape["carveout"])
+            if name in times:
+                return times[name]
+            apply(b, shape)
             b.sweep(a, 1)                      # warm-up
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            b.sweep(a, 1)
+            b.sweep(a, sweeps)
             e1.record(stream)
             e1.synchronize()
-            times[t] = e0.elapsed_time(e1)
+            times[name] = e0.elapsed_time(e1)
             if verbose:
-                print("autotune %s: %d threads %.2f ms" % (key, t, times[t]), flush=True)
-    best = min(times, key=times.get)
-    cache[key] = {"threads": int(best), "ms_per_sweep": times}
+                print("autotune %s: %s %.2f ms" % (key, name, times[name]), flush=True)
+            return times[name]
+
+        for knob, values in (("threads", SHAPES), ("ring", RINGS), ("carveout", CARVEOUTS)):
+            scores = {}
+            for v in values:
+                cand = dict(best, **{knob: v})
+                scores[v] = run(cand)
+            best[knob] = min(scores, key=scores.get)
+    cache[key] = {"shape": best, "ms_per_%d_sweeps" % sweeps: times}
     _save(cache)
-    return int(best)
+    return dict(best)

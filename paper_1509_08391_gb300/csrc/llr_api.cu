@@ -32,6 +32,7 @@ struct llr_ctx {
     int n_or = 4, block = 1;
     double beta_up = 1.5, beta_dn = 0.5;
     llr::LaunchCfg cfg;
+    int last_launch[5] = {0, 0, 0, 0, 0};   // threads, fast math, ring, carve-out, grid
     unsigned long long wait_limit_ns = 20000000000ull;
     unsigned *d_sync = nullptr;      // work queue of the persistent kernel: 2 + n words
     int *d_order = nullptr;          // 0 .. n-1 (single-lattice launches point into it)
@@ -46,6 +47,7 @@ struct llr_ctx {
     // one captured Robbins-Monro step (memset, persistent kernel, step + 1)
     cudaGraphExec_t rm_graph = nullptr;
     int g_therm = -1, g_meas = -1, g_index0 = -1;
+    int g_shape[4] = {0, 0, 0, 0};   // launch shape the graph was captured with
     double *g_a = nullptr, *g_hist = nullptr;
     cudaStream_t capture_stream = nullptr;
 };
@@ -87,6 +89,21 @@ llr::KernelArgs base_args(llr_handle h)
     a.sync = h->d_sync;
     a.wait_limit_ns = h->wait_limit_ns;
     return a;
+}
+
+// Launch the persistent kernel with the handle's shape; remember the shape.
+cudaError_t launch(llr_handle h, const llr::KernelArgs &a, cudaStream_t st)
+{
+    int grid = 0;
+    const cudaError_t e = llr::launch_llr(a, h->cfg, st, &grid);
+    if (e == cudaSuccess && grid > 0) {
+        h->last_launch[0] = h->cfg.threads;
+        h->last_launch[1] = h->cfg.fast_math ? 1 : 0;
+        h->last_launch[2] = h->cfg.ring;
+        h->last_launch[3] = h->cfg.carveout;
+        h->last_launch[4] = grid;
+    }
+    return e;
 }
 
 // Error word of the persistent launches since the last check (nonzero: a
@@ -226,7 +243,7 @@ int llr_init_lattice(llr_handle *out, const llr_config *cfg, void *cuda_stream)
     LLR_CUDA(llr::launch_hot_start(h->d_lat, h->d_theta, n, max_half, h->stream));
     llr::KernelArgs a = base_args(h);
     a.program = llr::kProgResync;
-    LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
+    LLR_CUDA(launch(h, a, h->stream));
     LLR_CUDA(cudaStreamSynchronize(h->stream));
     if (cfg->max_approach > 0) return llr_approach(h, cfg->max_approach, nullptr);
     return LLR_OK;
@@ -240,7 +257,7 @@ int llr_approach(llr_handle h, int max_sweeps, int *sweeps_out)
     a.program = llr::kProgApproach;
     a.max_approach = max_sweeps;
     a.approach_sweeps = h->d_int;
-    LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
+    LLR_CUDA(launch(h, a, h->stream));
     if (sweeps_out)
         LLR_CUDA(cudaMemcpyAsync(sweeps_out, h->d_int, sizeof(int) * (size_t)h->n,
                                  cudaMemcpyDeviceToHost, h->stream));
@@ -268,7 +285,7 @@ int llr_sweep(llr_handle h, const double *a_host, int n_sweeps, int measure, dou
     a.measure = measure != 0;
     a.a_in = h->d_a;
     a.mean_out = h->d_mean;
-    LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
+    LLR_CUDA(launch(h, a, h->stream));
     if (dE_sum_out && measure)
         LLR_CUDA(cudaMemcpyAsync(dE_sum_out, h->d_mean, sizeof(double) * (size_t)h->n,
                                  cudaMemcpyDeviceToHost, h->stream));
@@ -302,7 +319,7 @@ int llr_pass(llr_handle h, int kind, const double *a_host, int class_mask)
                                  cudaMemcpyHostToDevice, h->stream));
         a.a_in = h->d_a;
     }
-    LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
+    LLR_CUDA(launch(h, a, h->stream));
     LLR_CUDA(cudaStreamSynchronize(h->stream));
     return check_queue(h);
 }
@@ -322,7 +339,7 @@ int llr_rm_step_dev(llr_handle h, int n_therm, int n_meas, int rm_index, const d
     a.a_in = a_in;
     a.a_out = a_out;
     a.mean_out = dE_mean_out;
-    LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
+    LLR_CUDA(launch(h, a, h->stream));
     return LLR_OK;
 }
 
@@ -354,8 +371,10 @@ int llr_rm_run(llr_handle h, int n_therm, int n_meas, int rm_index0, int n_steps
     if (int r = check_handle(h)) return r;
     if (!a_dev || n_therm < 0 || n_meas < 1 || rm_index0 < 0 || n_steps < 0)
         return fail(LLR_ERR_ARG, "bad arguments");
+    const int shape[4] = {h->cfg.threads, h->cfg.fast_math ? 1 : 0, h->cfg.ring, h->cfg.carveout};
     if (!h->rm_graph || h->g_therm != n_therm || h->g_meas != n_meas ||
-        h->g_index0 != rm_index0 || h->g_a != a_dev || h->g_hist != hist_dev) {
+        h->g_index0 != rm_index0 || h->g_a != a_dev || h->g_hist != hist_dev ||
+        std::memcmp(shape, h->g_shape, sizeof(shape)) != 0) {
         if (h->rm_graph) cudaGraphExecDestroy(h->rm_graph);
         h->rm_graph = nullptr;
         if (!h->capture_stream)
@@ -373,7 +392,7 @@ int llr_rm_run(llr_handle h, int n_therm, int n_meas, int rm_index0, int n_steps
         llr::prime_launch(h->cfg);
         cudaGraph_t g;
         LLR_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e1 = llr::launch_llr(a, h->cfg, h->capture_stream);
+        cudaError_t e1 = launch(h, a, h->capture_stream);
         cudaError_t e2 = llr::launch_step_increment(h->d_step, h->capture_stream);
         cudaError_t e3 = cudaStreamEndCapture(h->capture_stream, &g);
         LLR_CUDA(e1);
@@ -387,6 +406,7 @@ int llr_rm_run(llr_handle h, int n_therm, int n_meas, int rm_index0, int n_steps
         h->g_index0 = rm_index0;
         h->g_a = a_dev;
         h->g_hist = hist_dev;
+        std::memcpy(h->g_shape, shape, sizeof(shape));
     }
     LLR_CUDA(cudaMemsetAsync(h->d_step, 0, sizeof(int), h->stream));
     for (int k = 0; k < n_steps; ++k) LLR_CUDA(cudaGraphLaunch(h->rm_graph, h->stream));
@@ -411,19 +431,19 @@ int llr_rm_step_plain(llr_handle h, int n_therm, int n_meas, int rm_index, doubl
     for (int i = 0; i < h->n; ++i) {
         a.order = h->d_order + i;
         a.program = llr::kProgBegin;
-        LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
+        LLR_CUDA(launch(h, a, h->stream));
         for (int j = 0; j < n_therm + n_meas; ++j) {
             a.program = llr::kProgPass;
             a.pass_kind = 0;
-            LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
+            LLR_CUDA(launch(h, a, h->stream));
             a.pass_kind = 1;
-            for (int k = 0; k < h->n_or; ++k) LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
+            for (int k = 0; k < h->n_or; ++k) LLR_CUDA(launch(h, a, h->stream));
             a.program = llr::kProgFinish;
             a.measure = j >= n_therm;
-            LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
+            LLR_CUDA(launch(h, a, h->stream));
         }
         a.program = llr::kProgUpdate;
-        LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
+        LLR_CUDA(launch(h, a, h->stream));
     }
     LLR_CUDA(cudaMemcpyAsync(a_inout, h->d_a, sizeof(double) * (size_t)h->n,
                              cudaMemcpyDeviceToHost, h->stream));
@@ -484,7 +504,7 @@ int llr_set_muca_weight(llr_handle h, int n, double e0, double de, const double 
     tab[0] = 0.0;
     for (int k = 0; k < n; ++k) {
         if (!std::isfinite(a_host[k])) return fail(LLR_ERR_ARG, "non-finite slope");
-        tab[(size_t)k + 1] = tab[(size_t)k] + a_host[k] * de;   // eq. rhoguess at the edges
+        tab[(size_t)k + 1] = tab[(size_t)k] + a_host[k] * de;   // eq. (2.10) at the edges
         tab[(size_t)n + 1 + (size_t)k] = a_host[k];
     }
     if (h->d_muca && h->muca_n != n) {
@@ -529,7 +549,7 @@ int llr_muca_sweep(llr_handle h, int n_sweeps, double *E_out)
     a.muca_de = h->muca_de;
     a.muca_a0 = h->muca_a0;
     a.e_hist = E_out ? h->d_ehist : nullptr;
-    LLR_CUDA(llr::launch_llr(a, h->cfg, h->stream));
+    LLR_CUDA(launch(h, a, h->stream));
     if (E_out)
         LLR_CUDA(cudaMemcpyAsync(E_out, h->d_ehist, sizeof(double) * need, cudaMemcpyDeviceToHost,
                                  h->stream));
@@ -652,10 +672,29 @@ int llr_status(llr_handle h, int *out)
 int llr_set_kernel_config(llr_handle h, int threads, int fast_math)
 {
     if (int r = check_handle(h)) return r;
+    return llr_set_kernel_shape(h, threads, fast_math, h->cfg.ring, h->cfg.carveout);
+}
+
+int llr_set_kernel_shape(llr_handle h, int threads, int fast_math, int ring, int carveout)
+{
+    if (int r = check_handle(h)) return r;
     if (threads != 128 && threads != 160 && threads != 192 && threads != 256 && threads != 512)
         return fail(LLR_ERR_ARG, "threads must be 128, 160, 192, 256 or 512");
+    if (ring != 1 && ring != 2 && ring != 4) return fail(LLR_ERR_ARG, "ring must be 1, 2 or 4");
+    if (carveout != -1 && carveout != 50 && carveout != 75 && carveout != 100)
+        return fail(LLR_ERR_ARG, "carveout must be -1 (default), 50, 75 or 100");
     h->cfg.threads = threads;
     h->cfg.fast_math = fast_math != 0;
+    h->cfg.ring = ring;
+    h->cfg.carveout = carveout;
+    return LLR_OK;
+}
+
+int llr_get_last_launch(llr_handle h, int *out)
+{
+    if (int r = check_handle(h)) return r;
+    if (!out) return fail(LLR_ERR_ARG, "null out");
+    for (int k = 0; k < 5; ++k) out[k] = h->last_launch[k];
     return LLR_OK;
 }
 

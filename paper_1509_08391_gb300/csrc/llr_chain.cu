@@ -6,10 +6,10 @@
 // Paper: Langfeld, Lucini, Pellegrini, Rago (arXiv:1509.08391).
 //   Sec. 3.1      action E = sum_P cos(theta_P), plaquette angle
 //                 theta_munu(x) = theta_mu(x) + theta_nu(x+mu) - theta_mu(x+nu) - theta_nu(x)
-//   eqs. kk7-kk10 weight exp(-a E) on the closed window [E_lo, E_lo + dE],
+//   eqs. (2.13)-(2.16) weight exp(-a E) on the closed window [E_lo, E_lo + dE],
 //                 dE_meas = E - E_lo - dE/2
 //   Algorithm 1   n_therm + n_meas sweeps, measure after n_therm
-//   eq. kk21      a <- a + 12 <<dE>> / (dE^2 (n + 1))
+//   eq. (2.30)      a <- a + 12 <<dE>> / (dE^2 (n + 1))
 //
 // Design
 //   * Links are float32 angles, SoA by (direction, site parity), sites of a
@@ -272,16 +272,11 @@ struct Smem {
     LatState st;
     Stage<NWP> stage[kStages];
     long long red[NWP + 1];
-    // overrelaxation groups decided move by move: per-warp sums of dE and
-    // |dE| (two buffers, one per chunk parity), block-end / accept masks and
-    // the running energy
-    int or_sum[2][NWP + 1], or_abs[2][NWP + 1];
-    unsigned or_em[NWP + 1], or_acc[NWP + 1];
-    long long or_E;
     unsigned long long acc_cnt;
     unsigned long long cap_cnt;
     int item_lat, item_j, item_state;
-    int cw;   // the consumer warp of a heat-bath pass
+    int cw;     // the consumer warp of a heat-bath pass
+    int ring;   // stages of the ring in use (a power of two <= kStages)
 };
 
 // Producer side of one heat-bath class (MU, p): proposals and warp prefix
@@ -291,7 +286,8 @@ struct Smem {
 // consumer accepted the block it belongs to.
 template <int MU, int NWP, bool FAST>
 __device__ __noinline__ void produce_class(Smem<NWP> &sm, float *th, int p, float a_f,
-                                           uint32_t tag, int B, int h0, int count, int nchunk)
+                                           uint32_t tag, int B, int h0, int count, int nchunk,
+                                           int D)
 {
     constexpr int NT = (NWP + 1) * 32, CH = NWP * 32;
     // producer rank pt (0 .. CH-1) and producer warp pw: the warps other
@@ -326,7 +322,7 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, float *th, int p, floa
     }
     cp_async_commit();
     for (int ch = 0; ch < nchunk; ++ch) {
-        const int s = ch & (kStages - 1);
+        const int s = ch & (D - 1);
         const int local = ch * CH + pt;
         const bool valid = valid_n;
         const int site = site_n;
@@ -343,9 +339,9 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, float *th, int p, floa
             }
             cp_async_commit();
         }
-        if (ch >= kStages) {
+        if (ch >= D) {
             bar_sync(5 + s, NT);
-            flush(sm.stage[s], ch - kStages);
+            flush(sm.stage[s], ch - D);
         }
         cp_async_wait<1>();
         float thn = 0.0f;
@@ -392,8 +388,8 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, float *th, int p, floa
         if (lane == 0) stg.endmask[pw] = em;
         bar_arrive(1 + s, NT);
     }
-    for (int c = nchunk > kStages ? nchunk - kStages : 0; c < nchunk; ++c) {
-        const int s = c & (kStages - 1);
+    for (int c = nchunk > D ? nchunk - D : 0; c < nchunk; ++c) {
+        const int s = c & (D - 1);
         bar_sync(5 + s, NT);
         flush(sm.stage[s], c);
     }
@@ -454,16 +450,17 @@ __device__ __forceinline__ void staple_sum_regs(const float v[18], float &Sr, fl
     }
 }
 
-// Largest |dE| of an overrelaxation move: 2^-14 (2^18 in the fixed point of
-// the running energy).  The reflection keeps the local energy
+// Overrelaxation and the window.  A reflection keeps the local energy
 // |S| cos(theta + alpha) exactly; a move changes E only through float32
-// rounding -- the reflection axis alpha carries the staple sum's error
-// (~1e-6 / |S|), the stored angle its rounding -- well below 2^-14 at
-// |S| <= 6.  A group of n moves therefore changes E by less than n * 2^-14,
-// and a group whose running energy is farther than that from both window
-// edges cannot have a move refused by the window rule.  In the groups that
-// are decided move by move, a move whose float32 dE estimate exceeds the
-// bound is refused (a guard never expected to act).
+// rounding (the reflection axis alpha carries the staple sum's error, ~1e-6 /
+// |S|, the stored angle its rounding), and its float32 dE estimate is as
+// uncertain as that change.  So the running energy is not changed by
+// overrelaxation, and a block of a group is taken iff E -- the running energy
+// at the start of the group -- lies outside the window, or E + dE_block lies
+// inside it (reading R19).  Every |dE| is below 2^-14 (a move whose float32
+// estimate exceeds that is refused, a guard never expected to act), so while
+// E is outside the window, or inside and farther than B * 2^-14 from both
+// edges, every move is taken without evaluating a dE.
 constexpr float kOrDeltaMax = 6.103515625e-05f;   // 2^-14
 constexpr long long kOrDeltaMaxFx = 1ll << 18;
 constexpr int kOrRefused = (int)0x80000000;
@@ -496,15 +493,12 @@ __device__ __forceinline__ float overrelax_link(const float *th, const float *ow
 }
 
 // One overrelaxation group (the links of class (MU, p) with half-site index
-// in [h0, h0 + count)) whose running energy E is farther than count * 2^-14
-// from both window edges: E +- count 2^-14 lies inside the window (every move
-// is taken by the window rule) or entirely on one side outside it (outside,
-// reflections are always taken), so no decision depends on the moves' dE.
-// Every thread reflects its links and writes them directly; the running
-// energy is left as it is (the moves change E only by float32 rounding, which
-// the fresh energy at the end of the composite sweep takes up).  The
-// neighbours are plain loads: within a slab they mostly hit L1/L2, and with no
-// consumer to feed, the loads of many warps hide each other.
+// in [h0, h0 + count)) whose running energy E lies outside the window, or
+// inside and farther than B * 2^-14 from both edges: every move is taken by
+// the window rule, so no dE is needed.  Every thread reflects its links and
+// writes them directly.  The neighbours are plain loads: within a slab they
+// mostly hit L1/L2, and with no consumer to feed, the loads of many warps
+// hide each other.
 template <int MU, int NWP, bool FAST>
 __device__ __noinline__ void overrelax_class(Smem<NWP> &sm, float *th, int p, int h0, int count)
 {
@@ -519,17 +513,13 @@ __device__ __noinline__ void overrelax_class(Smem<NWP> &sm, float *th, int p, in
     }
 }
 
-// Window decisions of one 32-link group in link order, by the calling warp.
-// Lane k holds Pk, the inclusive prefix sum of dE over the group's links
-// 0..k; em marks the lanes that end a block (blocks of B links start at
-// multiples of B).  Rules: heat-bath (OR_RULE false) takes a block iff
-// dist(E + dE_block) <= dist(E), dist the distance from the closed window;
-// overrelaxation (OR_RULE true) takes a block iff E + dE_block lies in the
-// window or E does not (outside, a reflection, which keeps E in exact
-// arithmetic, is always taken).  Inside the window both reduce to: taken iff
-// the energy after the block is inside.  Returns the mask of taken block
+// Heat-bath window decisions of one 32-link group in link order, by the
+// calling warp.  Lane k holds Pk, the inclusive prefix sum of dE over the
+// group's links 0..k; em marks the lanes that end a block (blocks of B links
+// start at multiples of B).  A block is taken iff dist(E + dE_block) <=
+// dist(E), dist the distance from the closed window (inside the window: iff
+// the energy after the block is inside).  Returns the mask of taken block
 // ends and advances E.
-template <bool OR_RULE>
 __device__ __forceinline__ unsigned window_scan_group(long long Pk, unsigned em, int B,
                                                       long long &E, long long lo, long long hi)
 {
@@ -571,11 +561,7 @@ __device__ __forceinline__ unsigned window_scan_group(long long Pk, unsigned em,
             const long long Ea = E + (Pk - base);
             const long long Eb = Ea - bk;
             const bool mine = (rem >> lane) & 1u;
-            bool ok;
-            if (OR_RULE)
-                ok = dist_fx(Eb, lo, hi) > 0 || dist_fx(Ea, lo, hi) == 0;
-            else
-                ok = dist_fx(Ea, lo, hi) <= dist_fx(Eb, lo, hi);
+            const bool ok = dist_fx(Ea, lo, hi) <= dist_fx(Eb, lo, hi);
             const unsigned vm = __ballot_sync(kFull, mine && !ok);
             if (vm == 0u) {
                 const int last = 31 - __clz(rem);
@@ -596,48 +582,28 @@ __device__ __forceinline__ unsigned window_scan_group(long long Pk, unsigned em,
     return acc;
 }
 
-// One overrelaxation group whose running energy E is within count * 2^-14 of
-// a window edge, in chunks of NT links (one per thread), each in the cheapest
-// form that gives the window rule's decisions:
-//   * E farther than NT * 2^-14 from both edges: every move is taken, as in
-//     overrelax_class (no barrier, E unchanged);
-//   * otherwise every thread forms its link's move and float32 dE estimate;
-//     one barrier gives the chunk's sum of dE and of |dE| (per-warp
-//     reductions); if E +- sum|dE| stays clear of both edges (or entirely on
-//     one side outside), every move is taken and E takes up the sum;
-//   * only then are the moves decided in link order: warp prefix sums (staged
-//     in the heat-bath's stage buffer, unused during an overrelaxation pass),
-//     warp 0 scans the 32-link groups (window_scan_group), the threads write
-//     the taken moves and E takes up their dE.
-// Chunks of one group need no barrier between them: links of one class do
-// not interact.  E enters as an argument (the same in every thread) and
-// leaves in sm.or_E, which thread 0 has set to it before the call; returns
-// the number of moves this thread took.
+// One overrelaxation group whose running energy E is inside the window and
+// within B * 2^-14 of an edge: every thread forms its links' moves and float32
+// dE estimates;
+// the blocks of B links (starting at the group's first link; a block lies in
+// one warp) sum their dE with shuffles, and a block is taken iff E lies
+// outside the window or E + dE_block inside it.  Decisions are independent of
+// one another (E does not move), so no barrier is needed.  Returns the number
+// of moves this thread took.
 template <int MU, int NWP, bool FAST>
-__device__ __noinline__ int overrelax_class_scan(Smem<NWP> &sm, float *th, int p, int h0,
+__device__ __noinline__ int overrelax_class_near(Smem<NWP> &sm, float *th, int p, int h0,
                                                  int count, int B, long long E)
 {
     constexpr int NT = (NWP + 1) * 32;
     const int L = sm.st.L, half = sm.st.half;
     const uint32_t magic = sm.st.magic;
     const long long lo = sm.st.lo_fx, hi = sm.st.hi_fx;
-    const long long m = (long long)NT * kOrDeltaMaxFx;
+    const bool outside = E < lo || E > hi;
     float *own = th + (2 * MU + p) * half;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    long long *stP = reinterpret_cast<long long *>(g_stage_buf);
-    int taken = 0, par = 0;
+    int taken = 0;
     for (int c0 = 0; c0 < count; c0 += NT) {
-        const int local = c0 + tid;
+        const int local = c0 + threadIdx.x;
         const bool valid = local < count;
-        if ((E - m >= lo && E + m <= hi) || E + m < lo || E - m > hi) {
-            if (valid) {
-                int dfx;
-                own[h0 + local] =
-                    overrelax_link<MU, FAST, false>(th, own, half, L, magic, p, h0 + local, dfx);
-                ++taken;
-            }
-            continue;
-        }
         int dfx = 0;
         float tn = 0.0f;
         bool ok = false;
@@ -646,60 +612,14 @@ __device__ __noinline__ int overrelax_class_scan(Smem<NWP> &sm, float *th, int p
             ok = dfx != kOrRefused;
             if (!ok) dfx = 0;
         }
-        // |dfx| <= 2^18, so a warp's sums fit in 32 bits
-        const int ws = __reduce_add_sync(kFull, dfx);
-        const int wa = __reduce_add_sync(kFull, dfx < 0 ? -dfx : dfx);
-        if (lane == 0) {
-            sm.or_sum[par][warp] = ws;
-            sm.or_abs[par][warp] = wa;
+        long long d = dfx;   // the block's dE (lanes of one block are an aligned segment)
+        for (int o = 1; o < B; o <<= 1) d += __shfl_xor_sync(kFull, d, o);
+        const long long Eb = E + d;
+        if (valid && ok && (outside || (Eb >= lo && Eb <= hi))) {
+            own[h0 + local] = tn;
+            ++taken;
         }
-        __syncthreads();
-        long long cs = 0, ca = 0;
-#pragma unroll
-        for (int w = 0; w <= NWP; ++w) {
-            cs += sm.or_sum[par][w];
-            ca += sm.or_abs[par][w];
-        }
-        par ^= 1;
-        if ((E - ca >= lo && E + ca <= hi) || E + ca < lo || E - ca > hi) {
-            if (valid && ok) {
-                own[h0 + local] = tn;
-                ++taken;
-            }
-            E += cs;
-            continue;
-        }
-        long long P = dfx;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long y = __shfl_up_sync(kFull, P, o);
-            if (lane >= o) P += y;
-        }
-        const bool isend = valid && (((lane & (B - 1)) == B - 1) || local == count - 1);
-        const unsigned em = __ballot_sync(kFull, isend);
-        stP[tid] = P;
-        if (lane == 0) sm.or_em[warp] = em;
-        __syncthreads();
-        if (warp == 0) {
-            long long Ew = E;
-            for (int g = 0; g <= NWP; ++g) {
-                const unsigned acc = window_scan_group<true>(stP[g * 32 + lane], sm.or_em[g], B,
-                                                             Ew, lo, hi);
-                if (lane == 0) sm.or_acc[g] = acc;
-            }
-            if (lane == 0) sm.or_E = Ew;
-        }
-        __syncthreads();
-        if (valid && ok) {
-            const int eb = __ffs(em & ~((1u << lane) - 1u)) - 1;
-            if ((sm.or_acc[warp] >> eb) & 1u) {
-                own[h0 + local] = tn;
-                ++taken;
-            }
-        }
-        E = sm.or_E;
     }
-    if (threadIdx.x == 0) sm.or_E = E;
     return taken;
 }
 
@@ -707,19 +627,19 @@ __device__ __noinline__ int overrelax_class_scan(Smem<NWP> &sm, float *th, int p
 // order; publishes the accepted block ends of each group (the producers
 // write the angles).  Runs in the last warp.
 template <int NWP>
-__device__ __noinline__ void consume_class(Smem<NWP> &sm, int B, int nchunk)
+__device__ __noinline__ void consume_class(Smem<NWP> &sm, int B, int nchunk, int D)
 {
     constexpr int NT = (NWP + 1) * 32;
     const int lane = threadIdx.x & 31;
     long long E = sm.st.E_fx;
     const long long lo = sm.st.lo_fx, hi = sm.st.hi_fx;
     for (int ch = 0; ch < nchunk; ++ch) {
-        const int s = ch & (kStages - 1);
+        const int s = ch & (D - 1);
         bar_sync(1 + s, NT);
         Stage<NWP> &stg = sm.stage[s];
         for (int g = 0; g < NWP; ++g) {
             const unsigned acc =
-                window_scan_group<false>(stg.P[g * 32 + lane], stg.endmask[g], B, E, lo, hi);
+                window_scan_group(stg.P[g * 32 + lane], stg.endmask[g], B, E, lo, hi);
             if (lane == 0) stg.accmask[g] = acc;
         }
         bar_arrive(5 + s, NT);
@@ -728,8 +648,8 @@ __device__ __noinline__ void consume_class(Smem<NWP> &sm, int B, int nchunk)
 }
 
 // ln rho~ of the multicanonical weight at the fixed-point energy E: the
-// piecewise-linear function of eq. rhoguess on the table's intervals,
-// continued with the first / last slope beyond them (Sec. 2.6, eq. 4.1).
+// piecewise-linear function of eq. (2.10) on the table's intervals,
+// continued with the first / last slope beyond them (Sec. 2.6, eq. (2.50)).
 __device__ __forceinline__ double muca_lnrho(const KernelArgs &a, long long E_fx)
 {
     const double E = (double)E_fx * kInvFx;
@@ -748,7 +668,7 @@ __device__ __forceinline__ double muca_lnrho(const KernelArgs &a, long long E_fx
 // dropped and the rest is decided again.  Blocks of one link.
 template <int NWP>
 __device__ __noinline__ void consume_class_muca(Smem<NWP> &sm, int nchunk, int mu, int p,
-                                                const KernelArgs &args)
+                                                const KernelArgs &args, int D)
 {
     constexpr int NT = (NWP + 1) * 32, CH = NWP * 32;
     const int lane = threadIdx.x & 31;
@@ -758,7 +678,7 @@ __device__ __noinline__ void consume_class_muca(Smem<NWP> &sm, int nchunk, int m
     const double a0 = args.muca_a0;
     long long E = sm.st.E_fx;
     for (int ch = 0; ch < nchunk; ++ch) {
-        const int s = ch & (kStages - 1);
+        const int s = ch & (D - 1);
         bar_sync(1 + s, NT);
         Stage<NWP> &stg = sm.stage[s];
         for (int g = 0; g < NWP; ++g) {
@@ -817,15 +737,19 @@ __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t
     if (threadIdx.x == 0) sm.acc_cnt = 0ull;
     __syncthreads();
     const int half = sm.st.half, L = sm.st.L;
+    const int D = sm.ring;   // stages of the producer/consumer ring in use: 1, 2 or 4
     if (kind == 1) {
         // Overrelaxation: slab by slab (x3), all classes within a slab, so the
         // neighbours a slab's staples read are still in L2 from the class before.
         const int S = half / L;
         const long long lo = windowed ? sm.st.lo_fx : -(1ll << 62);
         const long long hi = windowed ? sm.st.hi_fx : (1ll << 62);
-        const long long bound = (long long)S * kOrDeltaMaxFx;
-        long long E = sm.st.E_fx;   // running energy, the same in every thread
-        int taken = 0;              // moves taken by this thread in decided groups
+        // a block's |dE| is below B 2^-14, so no block can be refused unless E
+        // is inside the window and within that of an edge
+        const long long bound = (long long)B * kOrDeltaMaxFx;
+        const long long E = sm.st.E_fx;   // the running energy; overrelaxation leaves it
+        const bool free_all = E < lo || E > hi || (E - bound >= lo && E + bound <= hi);
+        int taken = 0;              // moves taken by this thread in near-edge groups
         unsigned long long n_free = 0;
 #pragma unroll 1
         for (int t = 0; t < L; ++t) {
@@ -833,11 +757,7 @@ __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t
             for (int cls = 0; cls < 8; ++cls) {
                 if (!((class_mask >> cls) & 1)) continue;
                 const int p = cls & 1;
-                // no decision of this group can depend on its moves' dE if E
-                // moves by less than `bound` and stays on one side of each edge
-                const bool free_group =
-                    (E - bound >= lo && E + bound <= hi) || E + bound < lo || E - bound > hi;
-                if (free_group) {
+                if (free_all) {
                     switch (cls >> 1) {
                         case 0: overrelax_class<0, NWP, FAST>(sm, th, p, t * S, S); break;
                         case 1: overrelax_class<1, NWP, FAST>(sm, th, p, t * S, S); break;
@@ -845,27 +765,21 @@ __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t
                         default: overrelax_class<3, NWP, FAST>(sm, th, p, t * S, S); break;
                     }
                     n_free += (unsigned long long)S;
-                    __syncthreads();   // the next group reads the angles written here
                 } else {
-                    if (threadIdx.x == 0) sm.or_E = E;
                     switch (cls >> 1) {
-                        case 0: taken += overrelax_class_scan<0, NWP, FAST>(sm, th, p, t * S, S, B, E); break;
-                        case 1: taken += overrelax_class_scan<1, NWP, FAST>(sm, th, p, t * S, S, B, E); break;
-                        case 2: taken += overrelax_class_scan<2, NWP, FAST>(sm, th, p, t * S, S, B, E); break;
-                        default: taken += overrelax_class_scan<3, NWP, FAST>(sm, th, p, t * S, S, B, E); break;
+                        case 0: taken += overrelax_class_near<0, NWP, FAST>(sm, th, p, t * S, S, B, E); break;
+                        case 1: taken += overrelax_class_near<1, NWP, FAST>(sm, th, p, t * S, S, B, E); break;
+                        case 2: taken += overrelax_class_near<2, NWP, FAST>(sm, th, p, t * S, S, B, E); break;
+                        default: taken += overrelax_class_near<3, NWP, FAST>(sm, th, p, t * S, S, B, E); break;
                     }
-                    __syncthreads();
-                    E = sm.or_E;
                 }
+                __syncthreads();   // the next group reads the angles written here
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) taken += __shfl_down_sync(kFull, taken, o);
         if ((threadIdx.x & 31) == 0 && taken) atomicAdd(&sm.acc_cnt, (unsigned long long)taken);
-        if (threadIdx.x == 0) {
-            atomicAdd(&sm.acc_cnt, n_free);
-            sm.st.E_fx = E;
-        }
+        if (threadIdx.x == 0 && n_free) atomicAdd(&sm.acc_cnt, n_free);
         (void)NT;
     } else {
         // Heat-bath: one class at a time over the whole lattice, so the
@@ -878,15 +792,15 @@ __device__ void run_pass(Smem<NWP> &sm, float *th, int kind, float a_f, uint32_t
             const int mu = cls >> 1, p = cls & 1;
             if (consumer) {
                 if (kind == 2)
-                    consume_class_muca<NWP>(sm, nchunk, mu, p, *muca);
+                    consume_class_muca<NWP>(sm, nchunk, mu, p, *muca, D);
                 else
-                    consume_class<NWP>(sm, B, nchunk);
+                    consume_class<NWP>(sm, B, nchunk, D);
             } else {
                 switch (mu) {
-                    case 0: produce_class<0, NWP, FAST>(sm, th, p, a_f, tag, B, 0, half, nchunk); break;
-                    case 1: produce_class<1, NWP, FAST>(sm, th, p, a_f, tag, B, 0, half, nchunk); break;
-                    case 2: produce_class<2, NWP, FAST>(sm, th, p, a_f, tag, B, 0, half, nchunk); break;
-                    default: produce_class<3, NWP, FAST>(sm, th, p, a_f, tag, B, 0, half, nchunk); break;
+                    case 0: produce_class<0, NWP, FAST>(sm, th, p, a_f, tag, B, 0, half, nchunk, D); break;
+                    case 1: produce_class<1, NWP, FAST>(sm, th, p, a_f, tag, B, 0, half, nchunk, D); break;
+                    case 2: produce_class<2, NWP, FAST>(sm, th, p, a_f, tag, B, 0, half, nchunk, D); break;
+                    default: produce_class<3, NWP, FAST>(sm, th, p, a_f, tag, B, 0, half, nchunk, D); break;
                 }
             }
             __syncthreads();   // the next class reads the angles written here
@@ -1117,7 +1031,10 @@ __global__ void __launch_bounds__((NWP + 1) * 32, min_ctas<NWP>()) llr_kernel(Ke
     unsigned *err = args.sync;
     unsigned *counter = args.sync + 1;
     unsigned *done = args.sync + 2;
-    if (tid == 0) sm.cw = NWP;   // the consumer warp of a heat-bath pass: the last
+    if (tid == 0) {
+        sm.cw = NWP;   // the consumer warp of a heat-bath pass: the last
+        sm.ring = (args.ring == 1 || args.ring == 2) ? args.ring : kStages;
+    }
     __syncthreads();
     for (;;) {
         if (tid == 0) {
@@ -1356,35 +1273,48 @@ __global__ void from_canonical_kernel(const LatState *lat, float *theta, const f
 template <int NWP>
 constexpr size_t stage_bytes() { return 2u * kStaged * (NWP + 1) * 32 * sizeof(float); }
 
-// Resident CTAs of one kernel variant (queried once per process and device;
-// also raises the variant's dynamic shared memory limit on that device).
+// Resident CTAs of one kernel variant under a shared-memory carve-out
+// preference (carveout: percent of the unified L1/shared storage, or -1 for
+// the driver's default).  Queried once per process, device and carve-out; the
+// query also sets the variant's dynamic shared memory limit and carve-out (a
+// property of the kernel function in this process, so the last configured
+// carve-out of a variant applies to every handle that launches it).
 template <int NWP, bool FAST>
-int resident_ctas()
+int resident_ctas(int carveout)
 {
-    static int cached[64] = {0};
+    static int cached[64][4] = {};
+    static int applied[64] = {};   // carve-out index + 1 last applied per device
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
-    if (cached[dev] == 0) {
-        int per_sm = 0, sms = 0;
+    const int ci = carveout < 0 ? 0 : carveout <= 50 ? 1 : carveout <= 75 ? 2 : 3;
+    if (applied[dev] != ci + 1) {
         cudaFuncSetAttribute(llr_kernel<NWP, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)stage_bytes<NWP>());
+        const int pct = ci == 0 ? (int)cudaSharedmemCarveoutDefault : ci == 1 ? 50 : ci == 2 ? 75 : 100;
+        cudaFuncSetAttribute(llr_kernel<NWP, FAST>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             pct);
+        applied[dev] = ci + 1;
+    }
+    if (cached[dev][ci] == 0) {
+        int per_sm = 0, sms = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, llr_kernel<NWP, FAST>,
                                                       (NWP + 1) * 32, stage_bytes<NWP>());
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cached[dev] = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+        cached[dev][ci] = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
     }
-    return cached[dev];
+    return cached[dev][ci];
 }
 
 template <int NWP, bool FAST>
-cudaError_t launch_t(const KernelArgs &a, cudaStream_t s)
+cudaError_t launch_t(const KernelArgs &a, int carveout, cudaStream_t s, int *grid_out)
 {
     const bool multi = a.program == kProgSweeps || a.program == kProgRM || a.program == kProgMuca;
     const long long items = (long long)a.n_lat * (multi ? (a.n_therm + a.n_meas) : 1);
     if (items <= 0) return cudaSuccess;
-    const long long cap = resident_ctas<NWP, FAST>();
+    const long long cap = resident_ctas<NWP, FAST>(carveout);
     const int grid = (int)(items < cap ? items : cap);
+    if (grid_out) *grid_out = grid;
     // the item counter and the done counters; the error word sync[0] is left
     // alone (sticky until the host reads and clears it)
     cudaError_t e = cudaMemsetAsync(a.sync + 1, 0, sizeof(unsigned) * (size_t)(1 + a.n_lat), s);
@@ -1398,25 +1328,29 @@ cudaError_t launch_t(const KernelArgs &a, cudaStream_t s)
 void prime_launch(const LaunchCfg &cfg)
 {
     const bool f = cfg.fast_math != 0;
+    const int c = cfg.carveout;
     switch (cfg.threads) {
-        case 128: f ? resident_ctas<3, true>() : resident_ctas<3, false>(); break;
-        case 160: f ? resident_ctas<4, true>() : resident_ctas<4, false>(); break;
-        case 192: f ? resident_ctas<5, true>() : resident_ctas<5, false>(); break;
-        case 512: f ? resident_ctas<15, true>() : resident_ctas<15, false>(); break;
-        default: f ? resident_ctas<7, true>() : resident_ctas<7, false>(); break;
+        case 128: f ? resident_ctas<3, true>(c) : resident_ctas<3, false>(c); break;
+        case 160: f ? resident_ctas<4, true>(c) : resident_ctas<4, false>(c); break;
+        case 192: f ? resident_ctas<5, true>(c) : resident_ctas<5, false>(c); break;
+        case 512: f ? resident_ctas<15, true>(c) : resident_ctas<15, false>(c); break;
+        default: f ? resident_ctas<7, true>(c) : resident_ctas<7, false>(c); break;
     }
 }
 
-cudaError_t launch_llr(const KernelArgs &a, const LaunchCfg &cfg, cudaStream_t s)
+cudaError_t launch_llr(const KernelArgs &args, const LaunchCfg &cfg, cudaStream_t s, int *grid_out)
 {
-    if (a.n_lat <= 0) return cudaSuccess;
+    if (args.n_lat <= 0) return cudaSuccess;
+    KernelArgs a = args;
+    a.ring = cfg.ring;
     const bool f = cfg.fast_math != 0;
+    const int c = cfg.carveout;
     switch (cfg.threads) {
-        case 128: return f ? launch_t<3, true>(a, s) : launch_t<3, false>(a, s);
-        case 160: return f ? launch_t<4, true>(a, s) : launch_t<4, false>(a, s);
-        case 192: return f ? launch_t<5, true>(a, s) : launch_t<5, false>(a, s);
-        case 512: return f ? launch_t<15, true>(a, s) : launch_t<15, false>(a, s);
-        default: return f ? launch_t<7, true>(a, s) : launch_t<7, false>(a, s);
+        case 128: return f ? launch_t<3, true>(a, c, s, grid_out) : launch_t<3, false>(a, c, s, grid_out);
+        case 160: return f ? launch_t<4, true>(a, c, s, grid_out) : launch_t<4, false>(a, c, s, grid_out);
+        case 192: return f ? launch_t<5, true>(a, c, s, grid_out) : launch_t<5, false>(a, c, s, grid_out);
+        case 512: return f ? launch_t<15, true>(a, c, s, grid_out) : launch_t<15, false>(a, c, s, grid_out);
+        default: return f ? launch_t<7, true>(a, c, s, grid_out) : launch_t<7, false>(a, c, s, grid_out);
     }
 }
 

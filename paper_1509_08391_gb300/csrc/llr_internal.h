@@ -57,22 +57,27 @@ struct KernelArgs {
     int muca_n;
     double muca_e0, muca_de, muca_a0;
     double *e_hist;       // kProgMuca, nullable: e_hist[sweep * n_lat + lattice] = E
+    int ring;             // stages of the heat-bath ring in use (1, 2 or 4; set at launch)
 };
 
 // *step += 1 (the last node of a captured Robbins-Monro step).
 cudaError_t launch_step_increment(int *step, cudaStream_t s);
 
 struct LaunchCfg {
-    int threads = 256;    // 128, 256 or 512: one consumer warp, the rest producers
+    int threads = 256;    // 128, 160, 192, 256 or 512: one consumer warp, the rest producers
     bool fast_math = true;
+    int ring = 4;         // stages of the heat-bath producer/consumer ring in use: 1, 2 or 4
+    int carveout = -1;    // shared-memory carve-out preference in percent, -1 = default
 };
 
 // Query (and cache) the resident-CTA count of a kernel variant; call before a
 // stream capture so the capture itself makes no occupancy queries.
 void prime_launch(const LaunchCfg &cfg);
 
-// Reset the work queue and launch the persistent kernel (stream ordered).
-cudaError_t launch_llr(const KernelArgs &a, const LaunchCfg &cfg, cudaStream_t s);
+// Reset the work queue and launch the persistent kernel (stream ordered);
+// grid_out (nullable) receives the number of CTAs launched.
+cudaError_t launch_llr(const KernelArgs &a, const LaunchCfg &cfg, cudaStream_t s,
+                       int *grid_out = nullptr);
 
 // Hot start of every link of every lattice.
 cudaError_t launch_hot_start(LatState *lats, float *theta, int n_lat, int max_half,

@@ -2,10 +2,10 @@
 // 3 -> 64 -> 64 -> 64 -> 1 GELU multilayer perceptron mapping
 // (1/V, E/6V, dE/6V), V = L^4, to the slope a, with hand-written FP32
 // forward, backward and Adam kernels.  1/V is the volume feature because the
-// finite-volume corrections of a_k are O(1/V) (appendix, eq. kkk35).
+// finite-volume corrections of a_k are O(1/V) (appendix, eq. (A.12)).
 //
-// The paper's a_k are intrinsic quantities (Sec. 2.2, eq. kk2; appendix,
-// eqs. kkk34-kkk36), so a map learned on small volumes can predict the
+// The paper's a_k are intrinsic quantities (Sec. 2.2, eq. (2.5); appendix,
+// eqs. (A.11)-(A.13)), so a map learned on small volumes can predict the
 // slopes of larger ones, and Sec. 2.4 only asks the initial a to be close.
 //
 // Layout: one float array of parameters, W1 (3x64, row-major [in][out]),

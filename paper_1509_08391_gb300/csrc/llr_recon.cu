@@ -2,8 +2,8 @@
 // from the Robbins-Monro slopes a_k.
 //
 // Paper: Langfeld, Lucini, Pellegrini, Rago (arXiv:1509.08391).
-//   eqs. kk3a, kk3b  ln rho(c_{k+1}) - ln rho(c_k) = (c_{k+1} - c_k) (a_k + a_{k+1}) / 2
-//   eqs. l19, l20    Z(beta) = sum_k w rho(c_k) e^{beta c_k},
+//   eqs. (2.6), (2.7)  ln rho(c_{k+1}) - ln rho(c_k) = (c_{k+1} - c_k) (a_k + a_{k+1}) / 2
+//   eqs. (2.46), (2.47)    Z(beta) = sum_k w rho(c_k) e^{beta c_k},
 //                    <E^m> = sum_k w c_k^m rho(c_k) e^{beta c_k} / Z
 //   Sec. 3.4         C_V = <E^2> - <E>^2, beta_c at its maximum
 //

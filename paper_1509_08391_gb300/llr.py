@@ -32,6 +32,7 @@ EXPORTS = [
     "llr_mlp_set_norm", "llr_mlp_get_norm", "llr_mlp_predict", "llr_mlp_grad", "llr_mlp_fit",
     "llr_mlp_destroy", "llr_set_wait_limit", "llr_state_bytes", "llr_save_state",
     "llr_load_state", "llr_replica_exchange", "llr_set_muca_weight", "llr_muca_sweep",
+    "llr_set_kernel_shape", "llr_get_last_launch",
 ]
 NOALLOC_MAX_CENTRES = 65536
 
@@ -92,6 +93,8 @@ def load(path: str = LIB_PATH):
         "llr_observables": [I, P, P, I, P, P, P, P],
         "llr_cv_peak": [I, P, P, D, D, I, D, P],
         "llr_set_kernel_config": [P, I, I],
+        "llr_set_kernel_shape": [P, I, I, I, I],
+        "llr_get_last_launch": [P, P],
         "llr_destroy": [P],
         "llr_observables_noalloc": [I, P, P, I, P, P, P, P, P],
         "llr_mlp_create": [ctypes.POINTER(P), ctypes.c_uint64, P],
@@ -193,6 +196,17 @@ class Batch:
     # -------------------------------------------------------------- dynamics
     def set_kernel_config(self, threads=256, fast_math=True):
         _check(load().llr_set_kernel_config(self._h, int(threads), 1 if fast_math else 0))
+
+    def set_kernel_shape(self, threads=256, fast_math=True, ring=4, carveout=-1):
+        _check(load().llr_set_kernel_shape(self._h, int(threads), 1 if fast_math else 0,
+                                           int(ring), int(carveout)))
+
+    def last_launch(self):
+        """{threads, fast_math, ring, carveout, grid} of the last batched launch."""
+        out = np.zeros(5, dtype=np.int32)
+        _check(load().llr_get_last_launch(self._h, _ptr(out)))
+        return dict(zip(("threads", "fast_math", "ring", "carveout", "grid"),
+                        (int(v) for v in out)))
 
     def approach(self, max_sweeps):
         out = np.zeros(self.n, dtype=np.int32)

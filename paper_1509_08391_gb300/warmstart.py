@@ -14,7 +14,7 @@ Protocol
      worth (s / eps)^2 Robbins-Monro steps, s = 12 sigma / dE^2 being the
      spread of one step's estimate of a (sigma the noise of <<dE>>).
   3. At the target volume, the Robbins-Monro iteration starts from the
-     prediction with the gain 12 / (dE^2 (n + n0 + 1)) (eq. kk21 with the
+     prediction with the gain 12 / (dE^2 (n + n0 + 1)) (eq. (2.30) with the
      step count shifted by n0, still a Robbins-Monro schedule: sum c_n
      diverges, sum c_n^2 converges, Sec. 2.2).  The plain form starts from a
      naive a = -1 with n0 = 0 (Sec. 2.4 allows any initial a).
@@ -189,3 +189,72 @@ def compare(target: workloads.Workload, net, eps, n_rm, n_therm, n_meas, eps_sto
     return CompareResult(converged_step(m_naive[:n_rm + 1], eps_stop, hold),
                          converged_step(m_warm, eps_stop, hold), agree_n, agree_w,
                          t_warm / n_rm, n0, eps, err_n, err_w)
+
+
+@dataclass
+class ArmResult:
+    steps: list              # per interval: steps to the stopping rule (None: not met)
+    seconds_per_step: float  # device time of one Robbins-Monro step of the arm's batch
+    err_at_stop: np.ndarray  # per interval: |replica-mean a at its stopping step - a_ref|
+    err_curve: np.ndarray    # mean over intervals of |replica-mean a^(n) - a_ref|, n = 0..n_rm
+    hist: np.ndarray         # a after each step, (steps, lattices)
+
+    def converged(self):
+        return [s for s in self.steps if s is not None]
+
+    def intervals_per_s(self, n_rm):
+        """Intervals that met the rule, over the time until the last of them did
+        (all n_rm steps if some never did)."""
+        done = self.converged()
+        if not done:
+            return 0.0
+        n = max(done) if len(done) == len(self.steps) else n_rm
+        return len(done) / (self.seconds_per_step * n)
+
+
+def converge_arms(target: workloads.Workload, net, eps, n_rm, n_therm, n_meas, eps_stop=1e-4,
+                  hold=3, stream=None):
+    """The batched Robbins-Monro iteration at the target volume from the
+    learned warm start (gain offset n0) and from the naive start a = -1
+    (n0 = 0), every (interval, replica) chain in one persistent launch per
+    step (graph replays).  The naive run continues to 2 n_rm steps; its
+    final replica means are the reference a_ref (with their standard errors).
+    Returns (warm arm, naive arm, a_ref, a_ref standard errors, n0)."""
+    L, e6v, d6v = interval_features(target)
+    a_warm = net.predict(L, e6v, d6v)
+    n0 = gain_offset(float(np.median(target.dE)), n_meas, eps, n_rm)
+    a_naive = np.full(target.n_lattices, target.a0)
+    with llr.Batch.from_workload(target, stream=stream, max_approach=1000) as b:
+        h_naive, t_naive = run_rm(b, a_naive, n_therm, n_meas, 2 * n_rm)
+    with llr.Batch.from_workload(target, stream=stream, max_approach=1000) as b:
+        h_warm, t_warm = run_rm(b, a_warm, n_therm, n_meas, n_rm, rm_offset=n0)
+    _, ref_a, ref_err, _ = slopes_by_interval(target, h_naive[-1])
+    arms = []
+    for a0, hist, t, steps_run in ((a_warm, h_warm, t_warm, n_rm),
+                                   (a_naive, h_naive[:n_rm], t_naive, 2 * n_rm)):
+        _, m = replica_mean_history(target, np.vstack([a0[None, :], hist]))
+        stop = converged_step(m, eps_stop, hold)
+        at = np.array([abs(m[s if s is not None else n_rm, k] - ref_a[k])
+                       for k, s in enumerate(stop)])
+        arms.append(ArmResult(stop, t / steps_run, at, np.abs(m - ref_a[None, :]).mean(axis=1),
+                              hist))
+    return arms[0], arms[1], ref_a, ref_err, n0
+
+
+def plain_arm(target: workloads.Workload, interval_index, n_steps, n_therm, n_meas,
+              stream=None):
+    """The plain form (one lattice at a time, one launch per pass, no graph,
+    naive start) on the replicas of one interval for n_steps Robbins-Monro
+    steps, timed on the host clock.  Returns (final a of the replicas, wall
+    seconds)."""
+    import time as _time
+    ids = np.asarray(target.interval_id)
+    k = np.unique(ids)[interval_index]
+    sub = workloads.subset(target, list(np.nonzero(ids == k)[0]))
+    with llr.Batch.from_workload(sub, stream=stream, max_approach=1000) as b:
+        a = np.full(sub.n_lattices, sub.a0)
+        t0 = _time.perf_counter()
+        for n in range(n_steps):
+            a, _ = b.rm_step_plain(a, n_therm, n_meas, n)
+        dt = _time.perf_counter() - t0
+    return a, dt

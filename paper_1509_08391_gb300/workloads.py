@@ -148,7 +148,7 @@ def subset(w: Workload, idx) -> Workload:
                     dict(w.notes))
 
 
-# Energy ranges of the paper's volume study (Tab. SimDet): E/6V from E_min
+# Energy ranges of the paper's volume study (Table 1): E/6V from E_min
 # to E_max in 512 contiguous intervals; N_SW sweeps and N_RM Robbins-Monro
 # iterations per interval.
 PAPER_VOLUME_STUDY = {
@@ -164,9 +164,9 @@ PAPER_VOLUME_STUDY = {
 
 def paper_volume_study(L: int, replicas: int = 8, n_therm: int = 5, n_meas: int = 20,
                        n_rm: int = 0, n_int: int = 512) -> Workload:
-    """The paper's L^4 study (Tab. SimDet): n_int (512) contiguous intervals of
+    """The paper's L^4 study (Table 1): n_int (512) contiguous intervals of
     width dE = (E_max - E_min) / n_int over its E/6V range (other n_int: the
-    discretisation study, Tab. descaling), `replicas` independent chains per
+    discretisation study, Table 7), `replicas` independent chains per
     interval (the paper repeats each run N_B = 20 times), N_RM Robbins-Monro
     iterations (the paper's value when n_rm = 0).  Sweeps per iteration are
     composite sweeps (1 heat-bath + 4 overrelaxation passes)."""

@@ -3,12 +3,12 @@
 Two-dimensional U(1) with open boundaries has independent plaquettes: in a
 maximal tree gauge every plaquette angle is one free link, so under the Haar
 measure the plaquette angles are independent and uniform (Sec. 3.1 for the
-model; the appendix, eq. kkk4, gives the density of a sum of independent
+model; the appendix, eq. (A.3), gives the density of a sum of independent
 domains).  Hence
 
 * one plaquette at weight exp(beta cos p): <cos p> = I1(beta)/I0(beta);
 * two plaquettes: E = cos p1 + cos p2 with p1, p2 uniform, so every
-  restricted, reweighted moment of eqs. kk7-kk9 is a two-dimensional
+  restricted, reweighted moment of eqs. (2.13)-(2.15) is a two-dimensional
   integral over (p1, p2) that quadrature evaluates to ~1e-10.
 
 Nothing here calls the oracle.
@@ -51,7 +51,7 @@ def restricted_mean_2plaq(lo, hi, a):
 
 
 def llr_root_2plaq(lo, hi, bracket=(-30.0, 30.0)):
-    """The a solving <<E - lo - dE/2>>(a) = 0 (eq. kk11) for two plaquettes."""
+    """The a solving <<E - lo - dE/2>>(a) = 0 (eq. (2.17)) for two plaquettes."""
     c = 0.5 * (lo + hi)
     return optimize.brentq(lambda a: restricted_mean_2plaq(lo, hi, a) - c, *bracket,
                            xtol=1e-12)

@@ -210,7 +210,8 @@ def compare_class(w, i, kind, a_i, cls, g, tr, S_cls, alpha_cls, sweep, E0, repo
     angle -- or, for the heat-bath, another attempt of the sampler at a near
     tie (sampler_near_tie).  Every block decision is then replayed in link
     order with the FP64 dE of the candidates, the running energy following
-    the GPU's decisions: each decision must equal the window rule's, except
+    the GPU's decisions (overrelaxation leaves it, R19): each decision must
+    equal the window rule's, except
     near ties (the energy before or after the block within e_tie_at of an
     edge).  Until the first near tie the replayed energies must equal the
     oracle's own."""
@@ -252,6 +253,8 @@ def compare_class(w, i, kind, a_i, cls, g, tr, S_cls, alpha_cls, sweep, E0, repo
     d_gpu_b = np.bincount(blk, weights=np.where(alt, d_gpu, d_prop), minlength=nb)
     acc_tr = np.asarray(tr["accepted"])[::B][:nb]
     step = np.where(taken_b | (amb_b & acc_tr), d_gpu_b, 0.0)
+    if kind == 1:
+        step[:] = 0.0        # R19: overrelaxation does not move the running energy
     E_b = E0 + np.concatenate([[0.0], np.cumsum(step)[:-1]])
     rule = window_rule(kind, E_b, d_prop_b, lo, hi)
     decided = ~amb_b & ~alt_b

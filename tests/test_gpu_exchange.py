@@ -108,7 +108,7 @@ def test_bad_pairs_are_rejected():
 
 def test_slopes_with_exchange_agree_with_slopes_without():
     """Exchanges change how chains move between windows, not the root of
-    eq. kk11: per interval the replica-mean slope after the same Robbins-Monro
+    eq. (2.17): per interval the replica-mean slope after the same Robbins-Monro
     schedule agrees with and without exchanges within the combined spread."""
     R = 6
     w = workloads.overlapping_l4(replicas=R)

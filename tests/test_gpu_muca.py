@@ -1,4 +1,4 @@
-"""The multicanonical run (Sec. 2.6, eq. 4.1) on the GPU against the FP64
+"""The multicanonical run (Sec. 2.6, eq. (2.50)) on the GPU against the FP64
 oracle: each heat-bath class of the weight 1/rho~ from an identical state
 (same proposals, same Metropolis-Hastings decisions except near ties), the
 canonical limit of a linear ln rho~ for any proposal slope, and the errors."""

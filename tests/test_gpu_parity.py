@@ -72,7 +72,7 @@ def test_running_energy_does_not_drift_over_heat_bath_passes():
     energy at the last resync plus the accepted dE in float32); over one pass
     it must follow the FP64 energy of the links without a systematic drift,
     or the window the chain enforces is shifted against the one the
-    measurement of eq. kk10 assumes, and every a_k with it.  256 L = 8
+    measurement of eq. (2.16) assumes, and every a_k with it.  256 L = 8
     lattices in their windows, 8 heat-bath passes each: the mean drift per pass
     is bounded far below the -4.8e-4 a per-move bias of -3.5e-8 produced."""
     w = workloads.subset(workloads.paper_volume_study(8, replicas=1), range(0, 512, 2))

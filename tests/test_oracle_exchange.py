@@ -1,6 +1,6 @@
 """Pins of the oracle's replica exchange between overlapping intervals
 (Sec. 2.5): the exchange must leave the product of the two restricted
-ensembles (eqs. kk7-kk9) invariant, so with exchanges every interval still
+ensembles (eqs. (2.13)-(2.15)) invariant, so with exchanges every interval still
 samples its own restricted density exactly, and the exchange rate is the
 expectation of the Metropolis probability under that product."""
 import numpy as np
@@ -41,7 +41,7 @@ def _product_swap_rate(w1, w2, a1, a2, n=4_000_000, seed=11):
 def test_exchange_keeps_each_restricted_ensemble_exact():
     """Two overlapping windows on the 2-plaquette strip at very different
     slopes, one composite sweep of each chain and one exchange attempt per
-    round: each window's mean energy equals the quadrature of eq. kk9, and the
+    round: each window's mean energy equals the quadrature of eq. (2.15), and the
     exchange rate equals its expectation under the product ensemble."""
     g = _strip()
     w1, w2 = (0.3, 0.9), (0.6, 1.2)

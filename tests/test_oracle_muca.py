@@ -1,5 +1,5 @@
-"""Pins of the oracle's multicanonical update (Sec. 2.6, eq. 4.1): the
-weight 1/rho~ with rho~ the piecewise-exponential density of eq. rhoguess,
+"""Pins of the oracle's multicanonical update (Sec. 2.6, eq. (2.50)): the
+weight 1/rho~ with rho~ the piecewise-exponential density of eq. (2.10),
 heat-bath proposals at a fixed slope a0 corrected by Metropolis-Hastings.
 
 * With a linear ln rho~ (one slope a everywhere) the weight is exp(-a E),

@@ -192,7 +192,7 @@ def test_three_plaquette_quadrature_is_self_consistent():
 def test_three_plaquette_blocks_of_two_are_exact():
     """4x2 open strip (3 plaquettes): a slab of one class holds two links, so
     with B = 2 the window decides two-link blocks; the chain still reproduces
-    the restricted mean of eq. kk9."""
+    the restricted mean of eq. (2.15)."""
     lo, hi, a = 0.9, 1.6, -1.0
     g = oracle.Geom([4, 2], periodic=False)
     assert g.nplaq == 3
@@ -211,7 +211,7 @@ def test_three_plaquette_blocks_of_two_are_exact():
 
 @pytest.mark.parametrize("block,a", [(1, -1.0), (2, 2.0), (1, 4.0)])
 def test_two_plaquette_restricted_mean_is_exact(block, a):
-    """2x1 plaquette strip (7 links): the restricted chain reproduces eq. kk9."""
+    """2x1 plaquette strip (7 links): the restricted chain reproduces eq. (2.15)."""
     lo, hi = 0.5, 1.1
     g = oracle.Geom([3, 2], periodic=False)
     assert g.nplaq == 2 and int(g.exists().sum()) == 7
@@ -230,7 +230,7 @@ def test_two_plaquette_restricted_mean_is_exact(block, a):
 
 
 def test_two_plaquette_robbins_monro_converges_to_root():
-    """Algorithm 1 with eq. kk21 on the strip converges to the root of eq. kk11."""
+    """Algorithm 1 with eq. (2.30) on the strip converges to the root of eq. (2.17)."""
     lo, hi = 0.5, 1.1
     root = exact2d.llr_root_2plaq(lo, hi)
     g = oracle.Geom([3, 2], periodic=False)
@@ -268,7 +268,7 @@ def test_robbins_monro_step_matches_eq_kk21_on_the_exact_mean():
     """One Robbins-Monro step from a = root + 0.5 on the 2-plaquette strip, the
     chain equilibrated at that a first: averaged over replicas, the step equals
     12 (<<E>>(a) - E_lo - dE/2) / (dE^2 (n + 1)) with <<E>>(a) from the
-    quadrature of eq. kk9, for n = 0 and n = 3.  A wrong gain constant, sign
+    quadrature of eq. (2.15), for n = 0 and n = 3.  A wrong gain constant, sign
     or step offset moves the mean step by a factor of 2 or more."""
     lo, hi = 0.5, 1.1
     dE = hi - lo

@@ -9,7 +9,7 @@ from oracle import mlp, recon
 
 # ---------------------------------------------------------------- reconstruction
 def test_trapezium_is_exact_for_linear_slope():
-    """eq. kk3a: the trapezium rule integrates a linear a(E) exactly."""
+    """eq. (2.6): the trapezium rule integrates a linear a(E) exactly."""
     c = np.sort(np.random.default_rng(1).uniform(100.0, 300.0, 40))
     a0, a1 = -1.3, 2.5e-3
     ln = recon.lnrho_at_centres(c, a0 + a1 * c)
@@ -18,7 +18,7 @@ def test_trapezium_is_exact_for_linear_slope():
 
 
 def test_gaussian_density_observables():
-    """ln rho = -(E-mu)^2/(2 s^2): <E>_beta = mu + beta s^2 and C_V = s^2 (eqs. l19-l20)."""
+    """ln rho = -(E-mu)^2/(2 s^2): <E>_beta = mu + beta s^2 and C_V = s^2 (eqs. (2.46)-(2.47))."""
     mu, s = 900.0, 12.0
     c = np.linspace(mu - 40 * s, mu + 40 * s, 8001)
     a = -(c - mu) / s ** 2

@@ -7,7 +7,7 @@ from paper_1509_08391_gb300 import workloads
 
 
 def test_paper_volume_study_has_contiguous_intervals_over_the_table_range():
-    """Tab. SimDet at L = 8: 512 intervals of width (E_max - E_min) / 512 that
+    """Table 1 at L = 8: 512 intervals of width (E_max - E_min) / 512 that
     tile [E_min, E_max] with no gap and no overlap (Sec. 2.4, E_k = E_min + k dE)."""
     w = workloads.paper_volume_study(8, replicas=3)
     six_v = 6 * 8 ** 4
@@ -47,7 +47,7 @@ def test_exchange_pairs_are_disjoint_overlapping_neighbours():
 
 def test_reweighting_table_matches_the_oracle_density():
     """The benchmark's host-side ln rho~ (used to reweight multicanonical
-    samples, eq. 4.7) and the oracle's are two codings of eq. rhoguess with
+    samples, eq. (2.56)) and the oracle's are two codings of eq. (2.10) with
     linear tails: they agree inside, below and above the table."""
     import bench
     import oracle
