@@ -83,6 +83,8 @@ def parse():
                         "centres, then one row per replica) instead of a coarse LLR run")
     p.add_argument("--muca-chains", type=int, default=512)
     p.add_argument("--muca-sweeps", type=int, default=4000)
+    p.add_argument("--muca-thin", type=int, default=1,
+                   help="reweight every n-th sweep of each chain")
     p.add_argument("--uneven", action="store_true",
                    help="the uneven batch: L = 8, 12, 16 x 64 intervals, dE scaled with sqrt(V), "
                         "one persistent launch per Robbins-Monro step replayed from a CUDA graph, "
@@ -825,7 +827,14 @@ def run_muca(args):
     e_min, e_max = centres[0] - 0.5 * dE, centres[-1] + 0.5 * dE
     # multicanonical chains: hot start, approach into [E_min, E_max], then W = 1/rho~
     nc = args.muca_chains
-    wm = workloads.Workload("u1_4d_L%d_muca_x%d" % (L, nc), [L] * nc, [e_min] * nc, [e_max - e_min] * nc,
+    # half the chains start at the bottom of the range, half at the top (the
+    # approach stops where it enters its window: the first half approaches
+    # the whole range and enters at its lower end, the second half a window
+    # covering the top twentieth), so the bias of the starting point cancels
+    span = e_max - e_min
+    lo_start = [e_min if c < nc // 2 else e_max - 0.05 * span for c in range(nc)]
+    de_start = [span if c < nc // 2 else 0.05 * span for c in range(nc)]
+    wm = workloads.Workload("u1_4d_L%d_muca_x%d" % (L, nc), [L] * nc, lo_start, de_start,
                             list(range(nc)), [0] * nc, workloads.SEED_BASE + 40)
     a0 = float(a_k.mean())
     t0 = time.perf_counter()
@@ -850,8 +859,10 @@ def run_muca(args):
             elif e > e_max - 0.1 * span and state != 1:
                 trips += state == -1
                 state = 1
-    # reweighting (eq. (2.56)): a sample at E carries e^{beta E} / W(E) = e^{beta E + ln rho~(E)}
-    x = E.ravel()
+    # reweighting (eq. (2.56)): a sample at E carries e^{beta E} / W(E) = e^{beta E + ln rho~(E)};
+    # every muca_thin-th sweep (successive sweeps of a chain are strongly correlated)
+    Et = E[::max(1, args.muca_thin)]
+    x = Et.ravel()
     lr = lnrho_table(e_min, dE, a_k, x)
     betas = np.linspace(1.000, 1.016, 1601)
 
@@ -873,7 +884,7 @@ def run_muca(args):
     b_mu, cv_mu = peak(x, lr)
     # spread of the reweighted peak over independent groups of chains
     groups = np.array_split(np.arange(nc), 8)
-    grp = [peak(E[:, gidx].ravel(), lnrho_table(e_min, dE, a_k, E[:, gidx].ravel()))
+    grp = [peak(Et[:, gidx].ravel(), lnrho_table(e_min, dE, a_k, Et[:, gidx].ravel()))
            for gidx in groups]
     gb = np.array([g[0] for g in grp])
     gc = np.array([g[1] for g in grp])
@@ -881,6 +892,8 @@ def run_muca(args):
     E_mu_c = moments(b_llr, x, lr)[0] / six_v
     _, E1, _ = llr.observables(centres, a_k, [b_llr])
     out = {"metric": "multicanonical reweighting vs LLR reconstruction (Sec. 2.6)", "L": L,
+           "starts": "half the chains at the bottom of the range, half at the top",
+           "thin": max(1, args.muca_thin),
            "llr": dict(llr_info, intervals=int(n_int), dE=dE, beta_c=b_llr,
                        cv_peak=cv_llr / six_v ** 2),
            "muca": {"chains": nc, "sweeps": args.muca_sweeps, "a0": a0,
@@ -899,8 +912,8 @@ def run_muca(args):
         bl = sorted(PAPER_E_L12)
         _, E_llr, _ = llr.observables(centres, a_k, bl)
         for bb, el in zip(bl, E_llr):
-            vals = [moments(bb, E[:, gidx].ravel(),
-                            lnrho_table(e_min, dE, a_k, E[:, gidx].ravel()))[0] / six_v
+            vals = [moments(bb, Et[:, gidx].ravel(),
+                            lnrho_table(e_min, dE, a_k, Et[:, gidx].ravel()))[0] / six_v
                     for gidx in groups]
             rows.append({"beta": bb, "muca": moments(bb, x, lr)[0] / six_v,
                          "muca_err": float(np.std(vals, ddof=1) / np.sqrt(len(vals))),
