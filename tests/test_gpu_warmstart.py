@@ -45,3 +45,27 @@ def test_warm_start_beats_naive_start_at_L20():
     assert len(warm) >= len(naive)
     if warm and naive:
         assert np.median(warm) <= np.median(naive)
+
+
+def test_learned_start_gains_at_the_top_of_the_c4_range_at_L20():
+    """The learned start as configured for C4: the network is trained on the
+    method's own slopes at L = 8 ... 16 over E/6V in [0.58, 0.68] and starts
+    the Robbins-Monro iteration at L = 20 (R = 4, dE = 50).  Tested on the top
+    of that range (E/6V in [0.655, 0.68], 8 intervals), where the slope has
+    moved away from the naive a = -1 (a_ref ~ -1.02): the learned start is
+    closer to the reference run and the iteration stays closer over its first
+    steps.  The full measurement (128 intervals at L = 20 and L = 24) also
+    shows where it does not gain: in the middle of the range, where
+    a ~ -1.00 ... -1.01, a = -1 is as close, and at L = 24 the network
+    extrapolates worse than a = -1."""
+    data = warmstart.training_set(n_int=24, replicas=2, n_rm=40, n_therm=2, n_meas=8)
+    net, eps, loss = warmstart.fit_network(data)
+    target = workloads.warm_start_targets(20, replicas=4, n_int=8, e_lo=0.655, e_hi=0.68)
+    warm, naive, ref_a, ref_err, n0 = warmstart.converge_arms(target, net, eps, 20, 2, 8)
+    net.close()
+    print("\n[c4 top] start error learned %.4f naive %.4f; mean over 6 steps %.4f / %.4f"
+          % (warm.err_curve[0], naive.err_curve[0], np.mean(warm.err_curve[:6]),
+             np.mean(naive.err_curve[:6])))
+    assert np.all(np.isfinite(ref_a)) and np.mean(ref_a) < -1.01
+    assert warm.err_curve[0] < 0.6 * naive.err_curve[0]
+    assert np.mean(warm.err_curve[:6]) < np.mean(naive.err_curve[:6])
