@@ -50,6 +50,10 @@ def parse():
                         "intervals/s")
     p.add_argument("--no-converge", action="store_true",
                    help="skip the converged-intervals leg of the default run")
+    p.add_argument("--train-replicas", type=int, default=2,
+                   help="replicas per interval of the warm start's training runs (L = 8 ... 16)")
+    p.add_argument("--train-rm", type=int, default=40,
+                   help="Robbins-Monro steps of the warm start's training runs")
     p.add_argument("--c4", action="store_true",
                    help="learned warm start as configured: 128 intervals at L = 20 and 24")
     p.add_argument("--target-L", type=int, default=20)
@@ -434,8 +438,8 @@ def converge_leg(args, L=None, n_int=None, replicas=None, n_rm=None, plain=True)
     R = replicas or args.target_replicas
     n_rm = n_rm or args.n_rm
     t_all = time.perf_counter()
-    data = warmstart.training_set(n_int=24, replicas=2, n_rm=40, n_therm=args.n_therm,
-                                  n_meas=args.n_meas)
+    data = warmstart.training_set(n_int=24, replicas=args.train_replicas, n_rm=args.train_rm,
+                                  n_therm=args.n_therm, n_meas=args.n_meas)
     net, eps, loss = warmstart.fit_network(data)
     target = workloads.warm_start_targets(L, replicas=R, n_int=n_int)
     warm, naive, ref_a, ref_err, n0 = warmstart.converge_arms(target, net, eps, n_rm,
@@ -506,13 +510,14 @@ def run_c4(args):
     bld.build()
     from paper_1509_08391_gb300 import warmstart, workloads
     t_all = time.perf_counter()
-    data = warmstart.training_set(n_int=24, replicas=2, n_rm=40, n_therm=args.n_therm,
-                                  n_meas=args.n_meas)
+    data = warmstart.training_set(n_int=24, replicas=args.train_replicas, n_rm=args.train_rm,
+                                  n_therm=args.n_therm, n_meas=args.n_meas)
     net, eps, loss = warmstart.fit_network(data)
     res = {"metric": "learned warm start vs naive start (C4)", "n_therm": args.n_therm,
            "n_meas": args.n_meas, "n_rm": args.n_rm, "replicas": 4,
            "stopping_rule": "replica-mean |a(n+1)-a(n)| <= 1e-4 for 3 consecutive steps",
            "mlp": {"train_points": int(len(data["a"])), "holdout_rms_L16": eps,
+                   "train_replicas": args.train_replicas, "train_rm_steps": args.train_rm,
                    "final_loss": loss, "train_seconds": data["seconds"]}, "volumes": {}}
     bins = np.linspace(0.58, 0.68, 5)
     for L in (20, 24):
