@@ -16,6 +16,12 @@ Follows Sec. 2.2 and Sec. 2.3 of Langfeld, Lucini, Pellegrini, Rago
   of the (uniformly spaced) centres.
 * Sec. 3.4: C_V(beta) = <E^2> - <E>^2 and beta_c = argmax C_V, located by a
   grid scan and golden-section refinement.
+* Sec. 2.6, eq. (2.56): canonical averages from the samples E_i of a
+  multicanonical run with weight W = 1/rho~: sample i carries
+  exp(beta E_i) / W(E_i) = exp(beta E_i + ln rho~(E_i)), so
+  <E^m>(beta) = sum_i E_i^m exp(beta E_i + ln rho~(E_i)) / sum_i exp(...).
+  The ergodicity check of the same section counts tunnellings: passages of
+  a chain from the lowest to the highest part of the range or back.
 
 Everything is evaluated in log space (log-sum-exp) in FP64.
 """
@@ -54,24 +60,70 @@ def specific_heat(c, a, beta):
 
 def cv_peak(c, a, beta_lo, beta_hi, n_grid=2001, tol=1e-12):
     """beta_c and C_V(beta_c): grid scan, then golden-section search."""
+    return _peak(lambda b: specific_heat(c, a, b), beta_lo, beta_hi, n_grid, tol)
+
+
+def _peak(f, beta_lo, beta_hi, n_grid, tol):
+    """Maximum of f on [beta_lo, beta_hi]: the best of n_grid equally spaced
+    points, then golden-section search between its two neighbours."""
     betas = np.linspace(beta_lo, beta_hi, n_grid)
-    cv = np.array([specific_heat(c, a, b) for b in betas])
+    cv = np.array([f(b) for b in betas])
     i = int(np.argmax(cv))
     lo = betas[max(i - 1, 0)]
     hi = betas[min(i + 1, n_grid - 1)]
     g = (np.sqrt(5.0) - 1.0) / 2.0
     x1 = hi - g * (hi - lo)
     x2 = lo + g * (hi - lo)
-    f1 = specific_heat(c, a, x1)
-    f2 = specific_heat(c, a, x2)
+    f1 = f(x1)
+    f2 = f(x2)
     while hi - lo > tol:
         if f1 < f2:
             lo, x1, f1 = x1, x2, f2
             x2 = lo + g * (hi - lo)
-            f2 = specific_heat(c, a, x2)
+            f2 = f(x2)
         else:
             hi, x2, f2 = x2, x1, f1
             x1 = hi - g * (hi - lo)
-            f1 = specific_heat(c, a, x1)
+            f1 = f(x1)
     b = 0.5 * (lo + hi)
-    return b, specific_heat(c, a, b)
+    return b, f(b)
+
+
+def muca_moments(E, lnrho_E, beta):
+    """(<E>, <E^2>) at coupling beta from multicanonical samples E (any
+    shape), eq. (2.56); lnrho_E holds ln rho~ at each sample."""
+    E = np.asarray(E, dtype=np.float64).ravel()
+    lr = np.asarray(lnrho_E, dtype=np.float64).ravel()
+    x = beta * E + lr
+    w = np.exp(x - x.max())
+    s0 = w.sum()
+    return (w * E).sum() / s0, (w * E * E).sum() / s0
+
+
+def muca_specific_heat(E, lnrho_E, beta):
+    E1, E2 = muca_moments(E, lnrho_E, beta)
+    return E2 - E1 * E1
+
+
+def muca_cv_peak(E, lnrho_E, beta_lo, beta_hi, n_grid=401, tol=1e-10):
+    """beta_c and C_V(beta_c) of the reweighted samples (Sec. 2.6 with
+    Sec. 3.4): grid scan, then golden-section search."""
+    return _peak(lambda b: muca_specific_heat(E, lnrho_E, b), beta_lo, beta_hi, n_grid, tol)
+
+
+def tunnellings(E_chain, lo, hi):
+    """Number of tunnellings of one chain (Sec. 2.6): its energies in time
+    order; each passage from E < lo to E > hi, or from E > hi to E < lo,
+    counts once."""
+    count = 0
+    last = 0            # -1: last seen below lo, +1: above hi, 0: neither yet
+    for e in E_chain:
+        if e < lo:
+            if last == 1:
+                count += 1
+            last = -1
+        elif e > hi:
+            if last == -1:
+                count += 1
+            last = 1
+    return count
