@@ -68,6 +68,10 @@ def parse():
     p.add_argument("--phys-therm", type=int, default=5)
     p.add_argument("--phys-meas", type=int, default=20)
     p.add_argument("--phys-rm", type=int, default=0, help="0 = the paper's N_RM")
+    p.add_argument("--phys-start", choices=("hot", "cold", "mixed"), default="hot",
+                   help="start of every chain: hot (uniform links, windows approached from "
+                        "below), cold (all links 0, approached from above), or mixed (odd "
+                        "replicas cold)")
     p.add_argument("--phys-intervals", default="512",
                    help="intervals over the E range; a comma-separated list runs the "
                         "discretisation study (C_V peak against dE^2, Sec. 3.5)")
@@ -587,18 +591,35 @@ PAPER_CV_PEAK = {8: (0.000551, 2e-6), 10: (0.000384, 2e-6), 12: (0.0002971, 1.1e
                  20: (0.0002007, 4e-7)}
 
 
-def physics_study(L, replicas, n_therm, n_meas, n_rm, beta_window=(1.0, 1.016), n_int=512):
-    """The whole LLR path at the paper's volume-study parameters: hot start,
+def cold_replica(start, r):
+    """Whether replica r starts cold under --phys-start (hot, cold, or mixed:
+    odd replicas cold, even replicas hot)."""
+    return start == "cold" or (start == "mixed" and r % 2 == 1)
+
+
+def physics_study(L, replicas, n_therm, n_meas, n_rm, beta_window=(1.0, 1.016), n_int=512,
+                  start="hot"):
+    """The whole LLR path at the paper's volume-study parameters: start,
     approach, n_rm graph-replayed Robbins-Monro iterations of every
     (interval, replica) chain from a = -1, then per replica ln rho and the
-    specific-heat peak; returns the per-replica beta_c and var(E/6V) peak."""
+    specific-heat peak; returns the per-replica beta_c and var(E/6V) peak.
+    A hot start draws every link uniformly and approaches each window from
+    below (a quench at beta_up); a cold start sets every link to 0 (E = 6V)
+    and approaches from above (heating at beta_dn)."""
     import torch
     from paper_1509_08391_gb300 import llr, workloads
     w = workloads.paper_volume_study(L, replicas, n_therm, n_meas, n_rm, n_int=n_int)
     n = w.n_lattices
     stream = torch.cuda.Stream()
     t_all = time.perf_counter()
-    with llr.Batch.from_workload(w, stream=stream.cuda_stream, max_approach=5000) as b:
+    cold = [cold_replica(start, r) for r in w.replica_id]
+    with llr.Batch.from_workload(w, stream=stream.cuda_stream,
+                                 max_approach=0 if any(cold) else 5000) as b:
+        if any(cold):
+            zeros = np.zeros(4 * L ** 4, dtype=np.float32)
+            for i in np.nonzero(cold)[0]:
+                b.set_links(int(i), zeros)
+            b.approach(5000)
         a_dev = torch.full((n,), w.a0, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -630,6 +651,7 @@ def physics_study(L, replicas, n_therm, n_meas, n_rm, beta_window=(1.0, 1.016), 
                            n_grid=1601, tol=1e-10)
     upd = n * w.n_rm * (w.n_therm + w.n_meas) * (1 + w.n_or) * 4 * L ** 4
     return {"workload": w.name, "L": L, "intervals": n_int, "replicas": replicas, "dE": dE,
+            "start": start, "cold_replicas": [r for r in range(replicas) if cold_replica(start, r)],
             "E_over_6V": [lo.min() / six_v, (lo.max() + dE) / six_v],
             "n_therm": w.n_therm, "n_meas": w.n_meas, "n_rm": w.n_rm, "a0": w.a0,
             "status_ok": ok, "heat_bath_acceptance": float(st["hb_acc"].sum() / st["hb_tot"].sum()),
@@ -653,7 +675,7 @@ def run_physics(args):
         run_discretisation(args, L, n_list)
         return
     res = physics_study(L, args.phys_replicas, args.phys_therm, args.phys_meas, args.phys_rm,
-                        n_int=n_list[0])
+                        n_int=n_list[0], start=args.phys_start)
     a_rep, centres = res.pop("slopes"), res.pop("centres")
     if args.phys_save:
         np.save(args.phys_save, np.vstack([centres[None, :], a_rep]))
@@ -667,6 +689,25 @@ def run_physics(args):
             res[key]["paper"] = pv
             res[key]["paper_err"] = pe
             res[key]["deviation_sigma"] = (m - pv) / float(np.hypot(e, pe))
+    if args.phys_start == "mixed":
+        # the same statistics per kind of start, and the slopes' difference
+        cold = np.array([cold_replica("mixed", r) for r in range(R)])
+        res["by_start"] = {}
+        for name, sel in (("hot", ~cold), ("cold", cold)):
+            bc = np.asarray(res["beta_c_per_replica"])[sel]
+            cv = np.asarray(res["cv_peak_per_replica"])[sel]
+            res["by_start"][name] = {
+                "beta_c": float(bc.mean()), "beta_c_err": float(bc.std(ddof=1) / np.sqrt(bc.size)),
+                "cv_peak": float(cv.mean()), "cv_peak_err": float(cv.std(ddof=1) / np.sqrt(cv.size))}
+        da = a_rep[cold].mean(axis=0) - a_rep[~cold].mean(axis=0)
+        err = np.sqrt(a_rep[cold].var(axis=0, ddof=1) / cold.sum()
+                      + a_rep[~cold].var(axis=0, ddof=1) / (~cold).sum())
+        six_v = 6.0 * L ** 4
+        res["slopes_cold_minus_hot"] = {
+            "E_over_6V": [float(x) for x in centres[::32] / six_v],
+            "mean_diff_per_32": [float(x) for x in da.reshape(-1, 32).mean(axis=1)],
+            "z_per_32": [float(x) for x in (da.reshape(-1, 32).sum(axis=1)
+                                            / np.sqrt((err.reshape(-1, 32) ** 2).sum(axis=1)))]}
     res["metric"] = "beta_c(L) and C_V peak vs the paper (Table 2, Table 4)"
     print(json.dumps(res), flush=True)
 
@@ -712,15 +753,6 @@ PAPER_E_L12 = {1.006: ((0.60180, 6e-5), (0.601714, 8e-6)),
                1.01023: ((0.6349, 5e-4), (0.6352, 1e-4)),
                1.012: ((0.65685, 5e-5), (0.65687, 1e-5)),
                1.014: ((0.66018, 4e-5), (0.660230, 5e-6))}
-
-
-def lnrho_table(e0, de, a, E):
-    """ln rho~ of eq. (2.10) at energies E (numpy, for the analysis of the
-    multicanonical samples): 0 at e0, slope a[k] in interval k, the end slopes
-    beyond the table."""
-    lnr = np.concatenate([[0.0], np.cumsum(np.asarray(a) * de)])
-    k = np.clip(np.floor((E - e0) / de).astype(np.int64), 0, len(a) - 1)
-    return lnr[k] + np.asarray(a)[k] * (E - (e0 + k * de))
 
 
 def run_exchange(args):
@@ -794,10 +826,11 @@ def run_muca(args):
     """--muca: the ergodicity check of Sec. 2.6 at L = 8.  (1) LLR slopes of
     the paper's L = 8 range in 64 intervals (4 replicas, 300 Robbins-Monro
     steps); (2) independent multicanonical chains with W = 1/rho~ from the
-    replica-mean slopes; (3) the energy histogram over the range, the round
-    trips between its ends, and <E>, C_V(beta) reweighted from the
-    multicanonical samples with W^-1 (eq. (2.56)) against the LLR reconstruction
-    of the same slopes (eqs. (2.46)/(2.47))."""
+    replica-mean slopes; (3) the energy histogram over the range, the
+    tunnellings between its ends (llr_muca_tunnellings), and <E>, C_V(beta)
+    reweighted from the multicanonical samples with W^-1 (eq. (2.56);
+    llr_muca_reweight, llr_muca_cv_peak) against the LLR reconstruction of the
+    same slopes (eqs. (2.46)/(2.47))."""
     import torch
     torch.cuda.set_device(0)
     from paper_1509_08391_gb300 import build as bld
@@ -852,49 +885,23 @@ def run_muca(args):
     # (3) flatness over the table's range
     h, _ = np.histogram(E.ravel(), bins=np.linspace(e_min, e_max, 17))
     frac = h / h.mean()
-    # round trips between the lowest and the highest tenth of the range
+    # tunnellings between the lowest and the highest tenth of the range
     span = e_max - e_min
-    trips = 0
-    for c in range(nc):
-        state = 0
-        for e in E[:, c]:
-            if e < e_min + 0.1 * span and state != -1:
-                trips += state == 1
-                state = -1
-            elif e > e_max - 0.1 * span and state != 1:
-                trips += state == -1
-                state = 1
-    # reweighting (eq. (2.56)): a sample at E carries e^{beta E} / W(E) = e^{beta E + ln rho~(E)};
-    # every muca_thin-th sweep (successive sweeps of a chain are strongly correlated)
+    trips = int(llr.muca_tunnellings(E, e_min + 0.1 * span, e_max - 0.1 * span).sum())
+    # reweighting (eq. (2.56)) in the library: a sample at E carries
+    # e^{beta E} / W(E) = e^{beta E + ln rho~(E)}; every muca_thin-th sweep
+    # (successive sweeps of a chain are strongly correlated)
     Et = E[::max(1, args.muca_thin)]
-    x = Et.ravel()
-    lr = lnrho_table(e_min, dE, a_k, x)
-    betas = np.linspace(1.000, 1.016, 1601)
-
-    def moments(beta, xs, lrs):
-        lw = beta * xs + lrs
-        wgt = np.exp(lw - lw.max())
-        m1 = np.sum(wgt * xs) / wgt.sum()
-        m2 = np.sum(wgt * xs * xs) / wgt.sum()
-        return m1, m2 - m1 * m1
-
-    def peak(xs, lrs):
-        cv = np.array([moments(bb, xs, lrs)[1] for bb in betas[::8]])
-        i = int(np.argmax(cv))
-        fine = betas[max(0, 8 * i - 8):8 * i + 9]
-        cvf = np.array([moments(bb, xs, lrs)[1] for bb in fine])
-        j = int(np.argmax(cvf))
-        return float(fine[j]), float(cvf[j] / six_v ** 2)
-
-    b_mu, cv_mu = peak(x, lr)
+    b_mu, cv_mu = llr.muca_cv_peak(Et, e_min, dE, a_k, 1.0, 1.016, n_grid=201, tol=1e-7)
+    cv_mu /= six_v ** 2
     # spread of the reweighted peak over independent groups of chains
     groups = np.array_split(np.arange(nc), 8)
-    grp = [peak(Et[:, gidx].ravel(), lnrho_table(e_min, dE, a_k, Et[:, gidx].ravel()))
+    grp = [llr.muca_cv_peak(Et[:, gidx], e_min, dE, a_k, 1.0, 1.016, n_grid=201, tol=1e-7)
            for gidx in groups]
     gb = np.array([g[0] for g in grp])
-    gc = np.array([g[1] for g in grp])
+    gc = np.array([g[1] for g in grp]) / six_v ** 2
     b_llr, cv_llr = llr.cv_peak(centres, a_k, 1.0, 1.016, n_grid=1601, tol=1e-10)
-    E_mu_c = moments(b_llr, x, lr)[0] / six_v
+    E_mu_c = llr.muca_reweight(Et, e_min, dE, a_k, [b_llr])[0][0] / six_v
     _, E1, _ = llr.observables(centres, a_k, [b_llr])
     out = {"metric": "multicanonical reweighting vs LLR reconstruction (Sec. 2.6)", "L": L,
            "starts": "half the chains at the bottom of the range, half at the top",
@@ -905,7 +912,7 @@ def run_muca(args):
                     "heat_bath_acceptance": float(st["hb_acc"].sum() / st["hb_tot"].sum()),
                     "histogram_over_range": [float(f) for f in frac],
                     "histogram_max_dev": float(np.max(np.abs(frac - 1.0))),
-                    "round_trips": int(trips), "seconds": t_muca,
+                    "tunnellings": int(trips), "seconds": t_muca,
                     "beta_c": b_mu, "beta_c_err": float(gb.std(ddof=1) / np.sqrt(len(gb))),
                     "cv_peak": cv_mu, "cv_peak_err": float(gc.std(ddof=1) / np.sqrt(len(gc)))},
            "E_over_6V_at_llr_beta_c": {"muca": E_mu_c, "llr": float(E1[0] / six_v)},
@@ -916,11 +923,12 @@ def run_muca(args):
         rows = []
         bl = sorted(PAPER_E_L12)
         _, E_llr, _ = llr.observables(centres, a_k, bl)
-        for bb, el in zip(bl, E_llr):
-            vals = [moments(bb, Et[:, gidx].ravel(),
-                            lnrho_table(e_min, dE, a_k, Et[:, gidx].ravel()))[0] / six_v
-                    for gidx in groups]
-            rows.append({"beta": bb, "muca": moments(bb, x, lr)[0] / six_v,
+        E_all = llr.muca_reweight(Et, e_min, dE, a_k, bl)[0] / six_v
+        E_grp = np.array([llr.muca_reweight(Et[:, gidx], e_min, dE, a_k, bl)[0] / six_v
+                          for gidx in groups])
+        for j, (bb, el) in enumerate(zip(bl, E_llr)):
+            vals = E_grp[:, j]
+            rows.append({"beta": bb, "muca": float(E_all[j]),
                          "muca_err": float(np.std(vals, ddof=1) / np.sqrt(len(vals))),
                          "llr_same_slopes": float(el / six_v),
                          "paper_llr": PAPER_E_L12[bb][0], "paper_reweighting": PAPER_E_L12[bb][1]})

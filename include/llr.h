@@ -265,6 +265,46 @@ int llr_observables_noalloc(int n, const double *centres, const double *a, int n
 int llr_cv_peak(int n, const double *centres, const double *a, double beta_lo, double beta_hi,
                 int n_grid, double tol, double *out);
 
+/* Canonical averages from the samples of a multicanonical run (Sec. 2.6,
+ * eq. (2.56)).  A run with weight W = 1/rho~ (llr_muca_sweep) visits E_i;
+ * reweighted to the coupling beta, sample i carries
+ * exp(beta E_i) / W(E_i) = exp(beta E_i + ln rho~(E_i)), with ln rho~ the
+ * table of llr_set_muca_weight: 0 at e0, slope a[k] on [e0 + k de,
+ * e0 + (k + 1) de), the first / last slope beyond the n intervals.  For each
+ * of n_beta couplings, <E> and <E^2> over all samples, in FP64 log space on
+ * the device (sums over E - e0).
+ *   E: host double[n_samples] (any order: the chains' samples pooled);
+ *   a: host double[n]; beta: host double[n_beta];
+ *   E_out, E2_out: host double[n_beta].  Synchronous, default stream; the
+ *   call allocates and frees its device buffers (~16 bytes per sample).
+ *   Errors: LLR_ERR_ARG (n_samples < 1, n < 1, de <= 0, non-finite e0,
+ *   slope or beta, null array), LLR_ERR_CUDA. */
+int llr_muca_reweight(long long n_samples, const double *E, int n, double e0, double de,
+                      const double *a, int n_beta, const double *beta, double *E_out,
+                      double *E2_out);
+
+/* The specific-heat peak (Sec. 3.4) of the reweighted samples of
+ * llr_muca_reweight: C_V(beta) = <E^2> - <E>^2 on n_grid equally spaced
+ * couplings in [beta_lo, beta_hi], then golden-section search between the
+ * best grid point's neighbours to |interval| < tol.  Every evaluation is a
+ * reweighting of all samples on the device.  Arguments as llr_muca_reweight.
+ * out: host double[2] = {beta_c, C_V(beta_c)}.
+ * Errors: as llr_muca_reweight, and LLR_ERR_ARG for n_grid < 2,
+ * beta_hi <= beta_lo or tol <= 0. */
+int llr_muca_cv_peak(long long n_samples, const double *E, int n, double e0, double de,
+                     const double *a, double beta_lo, double beta_hi, int n_grid, double tol,
+                     double *out);
+
+/* Tunnellings of multicanonical chains, the ergodicity check of Sec. 2.6:
+ * E: host double[n_steps][n_chains], the energy of every chain after each
+ * sweep (the layout llr_muca_sweep writes); a passage of a chain from
+ * E < lo to E > hi, or from E > hi to E < lo, counts once (E = lo or hi
+ * counts as neither end).  out: host int[n_chains].  Synchronous.
+ * Errors: LLR_ERR_ARG (n_steps < 0, n_chains < 1, lo > hi, null array),
+ * LLR_ERR_CUDA. */
+int llr_muca_tunnellings(int n_steps, int n_chains, const double *E, double lo, double hi,
+                         int *out);
+
 /* Launch shape of the batched sweep kernel: threads per CTA (128, 160, 192,
  * 256 or 512; one warp scans the window decisions, the others propose; one
  * CTA owns one lattice) and fast_math (1: hardware sine/cosine

@@ -148,6 +148,19 @@ int ensure_links_buffer(llr_handle h, size_t n)
     return LLR_OK;
 }
 
+// The multicanonical weight table of eq. (2.10): tab[k] = ln rho~ at the
+// edge e0 + k de (0 at k = 0) for k = 0..n, then the n slopes.
+int muca_table(int n, double de, const double *a, std::vector<double> &tab)
+{
+    tab.assign(2 * (size_t)n + 1, 0.0);
+    for (int k = 0; k < n; ++k) {
+        if (!std::isfinite(a[k])) return fail(LLR_ERR_ARG, "non-finite slope");
+        tab[(size_t)k + 1] = tab[(size_t)k] + a[k] * de;
+        tab[(size_t)n + 1 + (size_t)k] = a[k];
+    }
+    return LLR_OK;
+}
+
 }  // namespace
 
 int llr::set_last_error(int code, const char *msg)
@@ -500,13 +513,8 @@ int llr_set_muca_weight(llr_handle h, int n, double e0, double de, const double 
     if (n < 1 || !a_host || !std::isfinite(e0) || !std::isfinite(de) || !(de > 0.0) ||
         !std::isfinite(a0))
         return fail(LLR_ERR_ARG, "need n >= 1 finite slopes, finite e0, de > 0 and finite a0");
-    std::vector<double> tab(2 * (size_t)n + 1);
-    tab[0] = 0.0;
-    for (int k = 0; k < n; ++k) {
-        if (!std::isfinite(a_host[k])) return fail(LLR_ERR_ARG, "non-finite slope");
-        tab[(size_t)k + 1] = tab[(size_t)k] + a_host[k] * de;   // eq. (2.10) at the edges
-        tab[(size_t)n + 1 + (size_t)k] = a_host[k];
-    }
+    std::vector<double> tab;
+    if (int r = muca_table(n, de, a_host, tab)) return r;
     if (h->d_muca && h->muca_n != n) {
         LLR_CUDA(cudaStreamSynchronize(h->stream));
         cudaFree(h->d_muca);
@@ -799,7 +807,144 @@ int check_centres(int n, const double *c, const double *a)
     return LLR_OK;
 }
 
+// Samples of a multicanonical run on the device with ln rho~ at each, and the
+// scratch of the reweighting kernels for up to kBetaBatch couplings a launch.
+struct MucaSamples {
+    static constexpr int kBetaBatch = 512;
+    DevBuf buf;
+    long long ns = 0;
+    int gx = 1;
+    double shift = 0.0;
+    double *E = nullptr, *lr = nullptr, *beta = nullptr, *part = nullptr, *E1 = nullptr,
+           *E2 = nullptr, *var = nullptr;
+};
+
+int muca_samples_init(MucaSamples &w, long long ns, const double *E, int n, double e0, double de,
+                      const double *a)
+{
+    if (ns < 1 || !E) return fail(LLR_ERR_ARG, "need n_samples >= 1 samples");
+    if (n < 1 || !a || !std::isfinite(e0) || !std::isfinite(de) || !(de > 0.0))
+        return fail(LLR_ERR_ARG, "need n >= 1 finite slopes, finite e0 and de > 0");
+    std::vector<double> tab;
+    if (int r = muca_table(n, de, a, tab)) return r;
+    int dev = 0, sms = 1;
+    LLR_CUDA(cudaGetDevice(&dev));
+    LLR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // sample blocks per coupling: two per SM, none without samples
+    const long long tiles = (ns + 255) / 256;
+    w.gx = (int)std::max(1LL, std::min(tiles, 2LL * sms));
+    w.ns = ns;
+    w.shift = e0;
+    const int nb = MucaSamples::kBetaBatch;
+    const size_t total = 2 * (size_t)ns + tab.size() + (size_t)nb * (4 * (size_t)w.gx + 4);
+    LLR_CUDA(cudaMalloc(&w.buf.p, sizeof(double) * total));
+    w.E = (double *)w.buf.p;
+    w.lr = w.E + ns;
+    double *dtab = w.lr + ns;
+    w.beta = dtab + tab.size();
+    w.part = w.beta + nb;
+    w.E1 = w.part + 4 * (size_t)w.gx * nb;
+    w.E2 = w.E1 + nb;
+    w.var = w.E2 + nb;
+    LLR_CUDA(cudaMemcpy(w.E, E, sizeof(double) * (size_t)ns, cudaMemcpyHostToDevice));
+    LLR_CUDA(cudaMemcpy(dtab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
+    LLR_CUDA(llr::launch_muca_lnrho(ns, w.E, dtab, dtab + n + 1, n, e0, de, w.lr,
+                                    (int)std::min(tiles, 8LL * sms), nullptr));
+    return LLR_OK;
+}
+
+// <E>, <E^2> and <E^2> - <E>^2 at nb couplings (host arrays; any output may
+// be null), kBetaBatch couplings per launch.
+int muca_moments(MucaSamples &w, int nb, const double *beta, double *E1, double *E2, double *var)
+{
+    for (int b0 = 0; b0 < nb; b0 += MucaSamples::kBetaBatch) {
+        const int m = std::min(MucaSamples::kBetaBatch, nb - b0);
+        LLR_CUDA(cudaMemcpy(w.beta, beta + b0, sizeof(double) * (size_t)m,
+                            cudaMemcpyHostToDevice));
+        LLR_CUDA(llr::launch_reweight(w.ns, w.E, w.lr, w.shift, m, w.beta, w.gx, w.part, w.E1,
+                                      w.E2, w.var, nullptr));
+        const size_t bytes = sizeof(double) * (size_t)m;
+        if (E1) LLR_CUDA(cudaMemcpy(E1 + b0, w.E1, bytes, cudaMemcpyDeviceToHost));
+        if (E2) LLR_CUDA(cudaMemcpy(E2 + b0, w.E2, bytes, cudaMemcpyDeviceToHost));
+        if (var) LLR_CUDA(cudaMemcpy(var + b0, w.var, bytes, cudaMemcpyDeviceToHost));
+    }
+    return LLR_OK;
+}
+
 }  // namespace
+
+int llr_muca_reweight(long long n_samples, const double *E, int n, double e0, double de,
+                      const double *a, int n_beta, const double *beta, double *E_out,
+                      double *E2_out)
+{
+    if (n_beta < 1 || !beta || !E_out || !E2_out) return fail(LLR_ERR_ARG, "bad beta arrays");
+    for (int i = 0; i < n_beta; ++i)
+        if (!std::isfinite(beta[i])) return fail(LLR_ERR_ARG, "non-finite beta");
+    MucaSamples w;
+    if (int r = muca_samples_init(w, n_samples, E, n, e0, de, a)) return r;
+    return muca_moments(w, n_beta, beta, E_out, E2_out, nullptr);
+}
+
+int llr_muca_cv_peak(long long n_samples, const double *E, int n, double e0, double de,
+                     const double *a, double beta_lo, double beta_hi, int n_grid, double tol,
+                     double *out)
+{
+    if (!out || n_grid < 2 || !std::isfinite(beta_lo) || !std::isfinite(beta_hi) ||
+        !(beta_hi > beta_lo) || !(tol > 0.0))
+        return fail(LLR_ERR_ARG, "bad peak-search arguments");
+    MucaSamples w;
+    if (int r = muca_samples_init(w, n_samples, E, n, e0, de, a)) return r;
+    // grid scan (Sec. 3.4), then golden-section search between the best
+    // grid point's neighbours; every C_V evaluation is one reweighting
+    std::vector<double> grid((size_t)n_grid), cv((size_t)n_grid);
+    const double step = (beta_hi - beta_lo) / (double)(n_grid - 1);
+    for (int i = 0; i < n_grid; ++i) grid[(size_t)i] = beta_lo + step * (double)i;
+    if (int r = muca_moments(w, n_grid, grid.data(), nullptr, nullptr, cv.data())) return r;
+    int best = 0;
+    for (int i = 1; i < n_grid; ++i)
+        if (cv[(size_t)i] > cv[(size_t)best]) best = i;
+    double lo = grid[(size_t)std::max(best - 1, 0)];
+    double hi = grid[(size_t)std::min(best + 1, n_grid - 1)];
+    auto f = [&](double b, double &v) { return muca_moments(w, 1, &b, nullptr, nullptr, &v); };
+    const double g = 0.6180339887498949;   // (sqrt 5 - 1) / 2
+    double x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo), f1 = 0.0, f2 = 0.0;
+    if (int r = f(x1, f1)) return r;
+    if (int r = f(x2, f2)) return r;
+    for (int it = 0; it < 200 && hi - lo > tol; ++it) {
+        if (f1 < f2) {
+            lo = x1;
+            x1 = x2;
+            f1 = f2;
+            x2 = lo + g * (hi - lo);
+            if (int r = f(x2, f2)) return r;
+        } else {
+            hi = x2;
+            x2 = x1;
+            f2 = f1;
+            x1 = hi - g * (hi - lo);
+            if (int r = f(x1, f1)) return r;
+        }
+    }
+    out[0] = 0.5 * (lo + hi);
+    return f(out[0], out[1]);
+}
+
+int llr_muca_tunnellings(int n_steps, int n_chains, const double *E, double lo, double hi,
+                         int *out)
+{
+    if (n_steps < 0 || n_chains < 1 || (n_steps > 0 && !E) || !out || std::isnan(lo) ||
+        std::isnan(hi) || !(lo <= hi))
+        return fail(LLR_ERR_ARG, "need n_steps >= 0, n_chains >= 1 and lo <= hi");
+    const size_t ne = (size_t)n_steps * (size_t)n_chains;
+    DevBuf b;
+    LLR_CUDA(cudaMalloc(&b.p, sizeof(double) * ne + sizeof(int) * (size_t)n_chains));
+    double *dE = (double *)b.p;
+    int *dout = (int *)(dE + ne);
+    if (ne) LLR_CUDA(cudaMemcpy(dE, E, sizeof(double) * ne, cudaMemcpyHostToDevice));
+    LLR_CUDA(llr::launch_tunnellings(n_steps, n_chains, dE, lo, hi, dout, nullptr));
+    LLR_CUDA(cudaMemcpy(out, dout, sizeof(int) * (size_t)n_chains, cudaMemcpyDeviceToHost));
+    return LLR_OK;
+}
 
 int llr_reconstruct_lnrho(int n, const double *centres, const double *a, double *ln_rho_out)
 {

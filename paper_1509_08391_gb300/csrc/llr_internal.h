@@ -114,4 +114,18 @@ cudaError_t launch_cv_peak(int n, const double *c, const double *a, double beta_
                            double beta_hi, int n_grid, double tol, double *out,
                            cudaStream_t s);
 
+// Multicanonical reweighting kernels (Sec. 2.6, eq. (2.56)): ln rho~ of the
+// table (lnr[n + 1] at the edges, slopes a[n]) at ns samples; moments of the
+// samples reweighted to n_beta couplings (device beta[n_beta]; gx sample
+// blocks per coupling, part = 4 gx n_beta doubles of scratch; outputs
+// device double[n_beta] or null); tunnellings of n_chains chains.
+cudaError_t launch_muca_lnrho(long long ns, const double *E, const double *lnr, const double *a,
+                              int n, double e0, double de, double *out, int grid,
+                              cudaStream_t s);
+cudaError_t launch_reweight(long long ns, const double *E, const double *lr, double shift,
+                            int n_beta, const double *beta, int gx, double *part, double *E1,
+                            double *E2, double *var, cudaStream_t s);
+cudaError_t launch_tunnellings(int n_steps, int n_chains, const double *E, double lo, double hi,
+                               int *out, cudaStream_t s);
+
 }  // namespace llr

@@ -6,6 +6,9 @@
 //   eqs. (2.46), (2.47)    Z(beta) = sum_k w rho(c_k) e^{beta c_k},
 //                    <E^m> = sum_k w c_k^m rho(c_k) e^{beta c_k} / Z
 //   Sec. 3.4         C_V = <E^2> - <E>^2, beta_c at its maximum
+//   Sec. 2.6, eq. (2.56)   multicanonical reweighting: a sample E_i of the run
+//                    with weight 1/rho~ carries exp(beta E_i + ln rho~(E_i));
+//                    tunnellings of a chain between the ends of the range
 //
 // Sizes are small (hundreds to thousands of intervals), so each quantity is
 // one CTA: a block-wide FP64 scan for ln rho, log-sum-exp reductions for the
@@ -172,7 +175,153 @@ __global__ void __launch_bounds__(kT) cv_peak_kernel(int n, const double *c, con
     }
 }
 
+// ---------------------------------------------------------------------------
+// Multicanonical reweighting (Sec. 2.6, eq. (2.56)).  The moments at beta are
+// log-space sums over all samples; they run over d = E - shift (shift = the
+// table start, close to the samples), so that <E^2> - <E>^2 keeps its digits.
+
+// ln rho~ of eq. (2.10) at E: lnr[k] = ln rho~(e0 + k de), slope a[k] on
+// [e0 + k de, e0 + (k + 1) de), the first / last slope beyond the table.
+__device__ __forceinline__ double lnrho_piecewise(const double *lnr, const double *a, int n,
+                                                  double e0, double de, double E)
+{
+    const double q = fmin(fmax(floor((E - e0) / de), 0.0), (double)(n - 1));
+    const int k = (int)q;
+    return lnr[k] + a[k] * (E - (e0 + (double)k * de));
+}
+
+__global__ void __launch_bounds__(kT) muca_lnrho_kernel(long long ns, const double *E,
+                                                        const double *lnr, const double *a,
+                                                        int n, double e0, double de,
+                                                        double *out)
+{
+    const long long stride = (long long)gridDim.x * kT;
+    for (long long i = (long long)blockIdx.x * kT + threadIdx.x; i < ns; i += stride)
+        out[i] = lnrho_piecewise(lnr, a, n, e0, de, E[i]);
+}
+
+// Block (x, y): coupling beta[y] over the samples of kT-wide tiles x,
+// x + gridDim.x, ...  Each thread keeps a running maximum m of the exponent
+// and rescales its sums when it grows; the block then brings its threads to
+// the block maximum M.  Writes (M, s0, s1, s2), s_j = sum d^j exp(x - M).
+__global__ void __launch_bounds__(kT) reweight_partial_kernel(long long ns, const double *E,
+                                                              const double *lr, double shift,
+                                                              const double *beta, double *part)
+{
+    __shared__ double red[kT / 32];
+    const double b = beta[blockIdx.y];
+    double m = -INFINITY, s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    const long long stride = (long long)gridDim.x * kT;
+    for (long long i = (long long)blockIdx.x * kT + threadIdx.x; i < ns; i += stride) {
+        const double e_i = E[i];
+        const double x = b * e_i + lr[i];
+        if (x > m) {
+            const double r = exp(m - x);      // 0 on a thread's first sample
+            s0 *= r;
+            s1 *= r;
+            s2 *= r;
+            m = x;
+        }
+        const double w = exp(x - m);
+        const double d = e_i - shift;
+        s0 += w;
+        s1 += d * w;
+        s2 += d * d * w;
+    }
+    const double M = block_max(m, red);
+    const double r = m == -INFINITY ? 0.0 : exp(m - M);
+    s0 = block_sum(s0 * r, red);
+    s1 = block_sum(s1 * r, red);
+    s2 = block_sum(s2 * r, red);
+    if (threadIdx.x == 0) {
+        double *p = part + 4 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x);
+        p[0] = M;
+        p[1] = s0;
+        p[2] = s1;
+        p[3] = s2;
+    }
+}
+
+// One block per coupling: combine the gx partials of reweight_partial_kernel.
+// E1 = <E>, var = <E^2> - <E>^2, E2 = <E^2> (any of them may be null).
+__global__ void __launch_bounds__(kT) reweight_combine_kernel(int gx, const double *part,
+                                                              double shift, double *E1,
+                                                              double *E2, double *var)
+{
+    __shared__ double red[kT / 32];
+    const double *p = part + 4 * (size_t)blockIdx.x * gx;
+    double m = -INFINITY;
+    for (int j = threadIdx.x; j < gx; j += kT) m = fmax(m, p[4 * j]);
+    m = block_max(m, red);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int j = threadIdx.x; j < gx; j += kT) {
+        const double mj = p[4 * j];
+        if (mj == -INFINITY) continue;        // a block without samples
+        const double r = exp(mj - m);
+        s0 += r * p[4 * j + 1];
+        s1 += r * p[4 * j + 2];
+        s2 += r * p[4 * j + 3];
+    }
+    s0 = block_sum(s0, red);
+    s1 = block_sum(s1, red);
+    s2 = block_sum(s2, red);
+    if (threadIdx.x == 0) {
+        const double u = s1 / s0, v = s2 / s0 - u * u, e1 = shift + u;
+        if (E1) E1[blockIdx.x] = e1;
+        if (var) var[blockIdx.x] = v;
+        if (E2) E2[blockIdx.x] = e1 * e1 + v;
+    }
+}
+
+// Tunnellings of each chain (Sec. 2.6): E[t][c] in time order t; a passage
+// from E < lo to E > hi or back counts once.  One thread per chain, the
+// loads of a time step coalesced across chains.
+__global__ void __launch_bounds__(kT) tunnelling_kernel(int n_steps, int n_chains,
+                                                        const double *E, double lo, double hi,
+                                                        int *out)
+{
+    const int c = blockIdx.x * kT + threadIdx.x;
+    if (c >= n_chains) return;
+    int count = 0, last = 0;
+    for (int t = 0; t < n_steps; ++t) {
+        const double e = E[(size_t)t * n_chains + c];
+        if (e < lo) {
+            count += last == 1;
+            last = -1;
+        } else if (e > hi) {
+            count += last == -1;
+            last = 1;
+        }
+    }
+    out[c] = count;
+}
+
 }  // namespace
+
+cudaError_t launch_muca_lnrho(long long ns, const double *E, const double *lnr, const double *a,
+                              int n, double e0, double de, double *out, int grid,
+                              cudaStream_t s)
+{
+    muca_lnrho_kernel<<<grid, kT, 0, s>>>(ns, E, lnr, a, n, e0, de, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reweight(long long ns, const double *E, const double *lr, double shift,
+                            int n_beta, const double *beta, int gx, double *part, double *E1,
+                            double *E2, double *var, cudaStream_t s)
+{
+    if (n_beta <= 0) return cudaSuccess;
+    reweight_partial_kernel<<<dim3(gx, n_beta), kT, 0, s>>>(ns, E, lr, shift, beta, part);
+    reweight_combine_kernel<<<n_beta, kT, 0, s>>>(gx, part, shift, E1, E2, var);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tunnellings(int n_steps, int n_chains, const double *E, double lo, double hi,
+                               int *out, cudaStream_t s)
+{
+    tunnelling_kernel<<<(n_chains + kT - 1) / kT, kT, 0, s>>>(n_steps, n_chains, E, lo, hi, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_lnrho(int n, const double *c, const double *a, double *out, cudaStream_t s)
 {

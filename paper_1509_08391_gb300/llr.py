@@ -32,7 +32,8 @@ EXPORTS = [
     "llr_mlp_set_norm", "llr_mlp_get_norm", "llr_mlp_predict", "llr_mlp_grad", "llr_mlp_fit",
     "llr_mlp_destroy", "llr_set_wait_limit", "llr_state_bytes", "llr_save_state",
     "llr_load_state", "llr_replica_exchange", "llr_set_muca_weight", "llr_muca_sweep",
-    "llr_set_kernel_shape", "llr_get_last_launch",
+    "llr_set_kernel_shape", "llr_get_last_launch", "llr_muca_reweight", "llr_muca_cv_peak",
+    "llr_muca_tunnellings",
 ]
 NOALLOC_MAX_CENTRES = 65536
 
@@ -92,6 +93,9 @@ def load(path: str = LIB_PATH):
         "llr_reconstruct_lnrho": [I, P, P, P],
         "llr_observables": [I, P, P, I, P, P, P, P],
         "llr_cv_peak": [I, P, P, D, D, I, D, P],
+        "llr_muca_reweight": [ctypes.c_longlong, P, I, D, D, P, I, P, P, P],
+        "llr_muca_cv_peak": [ctypes.c_longlong, P, I, D, D, P, D, D, I, D, P],
+        "llr_muca_tunnellings": [I, I, P, D, D, P],
         "llr_set_kernel_config": [P, I, I],
         "llr_set_kernel_shape": [P, I, I, I, I],
         "llr_get_last_launch": [P, P],
@@ -352,6 +356,39 @@ def cv_peak(centres, a, beta_lo, beta_hi, n_grid=2001, tol=1e-12):
     _check(load().llr_cv_peak(len(c), _ptr(c), _ptr(a), float(beta_lo), float(beta_hi),
                               int(n_grid), float(tol), _ptr(out)))
     return float(out[0]), float(out[1])
+
+
+def muca_reweight(E, e0, de, a, betas):
+    """<E>, <E^2> of multicanonical samples E (any shape, pooled) reweighted
+    to each coupling (llr_muca_reweight, eq. (2.56))."""
+    x = np.ascontiguousarray(np.ravel(E), dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(np.atleast_1d(betas), dtype=np.float64)
+    e1, e2 = np.zeros_like(b), np.zeros_like(b)
+    _check(load().llr_muca_reweight(x.size, _ptr(x), len(a), float(e0), float(de), _ptr(a),
+                                    len(b), _ptr(b), _ptr(e1), _ptr(e2)))
+    return e1, e2
+
+
+def muca_cv_peak(E, e0, de, a, beta_lo, beta_hi, n_grid=401, tol=1e-10):
+    """(beta_c, C_V(beta_c)) of reweighted multicanonical samples (llr_muca_cv_peak)."""
+    x = np.ascontiguousarray(np.ravel(E), dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    out = np.zeros(2)
+    _check(load().llr_muca_cv_peak(x.size, _ptr(x), len(a), float(e0), float(de), _ptr(a),
+                                   float(beta_lo), float(beta_hi), int(n_grid), float(tol),
+                                   _ptr(out)))
+    return float(out[0]), float(out[1])
+
+
+def muca_tunnellings(E, lo, hi):
+    """Tunnellings per chain of E[step][chain] between E < lo and E > hi
+    (llr_muca_tunnellings)."""
+    x = np.ascontiguousarray(np.atleast_2d(E), dtype=np.float64)
+    out = np.zeros(x.shape[1], dtype=np.int32)
+    _check(load().llr_muca_tunnellings(x.shape[0], x.shape[1], _ptr(x), float(lo), float(hi),
+                                       _ptr(out)))
+    return out
 
 
 def observables_noalloc(centres_dev, a_dev, beta_dev, lnZ_dev, E_dev, E2_dev, stream=None):

@@ -43,19 +43,3 @@ def test_exchange_pairs_are_disjoint_overlapping_neighbours():
             seen_pairs.add((i, j))
     # the two parities together try every neighbouring pair once
     assert len(seen_pairs) == 3 * (7 - 1)
-
-
-def test_reweighting_table_matches_the_oracle_density():
-    """The benchmark's host-side ln rho~ (used to reweight multicanonical
-    samples, eq. (2.56)) and the oracle's are two codings of eq. (2.10) with
-    linear tails: they agree inside, below and above the table."""
-    import bench
-    import oracle
-    rng = np.random.default_rng(3)
-    a = -1.0 + 0.05 * rng.standard_normal(24)
-    e0, de = 900.0, 3.5
-    w = oracle.MucaWeight(e0, de, a)
-    E = np.concatenate([[e0, e0 + 24 * de], rng.uniform(e0 - 20.0, e0 + 24 * de + 20.0, 200)])
-    mine = bench.lnrho_table(e0, de, a, E)
-    ref = np.array([w.lnrho(x) for x in E])
-    assert np.allclose(mine, ref, rtol=0, atol=1e-9)
