@@ -81,6 +81,18 @@ def parse():
                    help="replica exchange at the paper's L = 8 range (Sec. 2.5): half-overlapping "
                         "windows, one exchange round after every Robbins-Monro step; beta_c and "
                         "the C_V peak against the paper, exchange rates")
+    p.add_argument("--canonical", action="store_true",
+                   help="canonical <E>/6V in one pure phase (a heat-bath + overrelaxation run at "
+                        "a = -beta in a window several fluctuation widths wide), against the "
+                        "paper's L = 12 table beside Fig. 2")
+    p.add_argument("--canon-L", type=int, default=12)
+    p.add_argument("--canon-beta", type=float, default=1.014)
+    p.add_argument("--canon-window", default="0.64,0.70",
+                   help="E/6V bounds of the window (wide enough to hold the phase's peak)")
+    p.add_argument("--canon-start", choices=("hot", "cold"), default="cold")
+    p.add_argument("--canon-chains", type=int, default=2048)
+    p.add_argument("--canon-therm", type=int, default=500)
+    p.add_argument("--canon-blocks", type=int, default=40, help="measured blocks of 100 sweeps")
     p.add_argument("--muca", action="store_true",
                    help="multicanonical check of Sec. 2.6 at L = 8: LLR slopes of a coarse volume "
                         "study, then chains with the weight 1/rho~: histogram flatness, round "
@@ -936,6 +948,56 @@ def run_muca(args):
     print(json.dumps(out), flush=True)
 
 
+def run_canonical(args):
+    """--canonical: <E>/6V of one pure phase at coupling beta.  Every chain
+    runs composite sweeps at a = -beta restricted to a window of E/6V several
+    canonical fluctuation widths wide around the phase's peak (so the other
+    phase, and the tunnelling between them, are cut away); a hot start draws
+    every link uniformly and approaches the window from below (a quench at
+    beta_up), a cold start sets every link to 0 and approaches from above.
+    After n_therm sweeps, blocks of 100 measured sweeps (llr_sweep with
+    measure); the error is the spread of the per-chain means over the
+    independent chains; the block means of the first and second half show
+    whether the chains still drift."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1509_08391_gb300 import build as bld
+    bld.build()
+    from paper_1509_08391_gb300 import llr, workloads
+    L, nc, beta = args.canon_L, args.canon_chains, args.canon_beta
+    e_lo, e_hi = (float(x) for x in args.canon_window.split(","))
+    six_v = 6.0 * L ** 4
+    lo, de = e_lo * six_v, (e_hi - e_lo) * six_v
+    w = workloads.Workload("u1_4d_L%d_canonical_b%g_x%d" % (L, beta, nc), [L] * nc, [lo] * nc,
+                           [de] * nc, list(range(nc)), [0] * nc, workloads.SEED_BASE + 77)
+    cold = args.canon_start == "cold"
+    t0 = time.perf_counter()
+    with llr.Batch.from_workload(w, max_approach=0 if cold else 5000) as b:
+        if cold:
+            zeros = np.zeros(4 * L ** 4, dtype=np.float32)
+            for i in range(nc):
+                b.set_links(i, zeros)
+            b.approach(5000)
+        b.sweep(-beta, args.canon_therm)
+        blocks = [b.sweep(-beta, 100, measure=True) / 100.0 + lo + 0.5 * de
+                  for _ in range(args.canon_blocks)]
+        ok = bool(np.all(b.status() == 0))
+    e = np.array(blocks) / six_v                  # [block, chain]
+    per_chain = e.mean(axis=0)
+    half = args.canon_blocks // 2
+    out = {"metric": "canonical <E>/6V in one pure phase", "L": L, "beta": beta,
+           "window_E_over_6V": [e_lo, e_hi], "start": args.canon_start, "chains": nc,
+           "n_therm": args.canon_therm, "measured_sweeps": 100 * args.canon_blocks,
+           "status_ok": ok, "E_over_6V": float(per_chain.mean()),
+           "err": float(per_chain.std(ddof=1) / np.sqrt(nc)),
+           "first_half": float(e[:half].mean()), "second_half": float(e[half:].mean()),
+           "block_range": [float(e.min()), float(e.max())],
+           "seconds": time.perf_counter() - t0}
+    if L == 12 and beta in PAPER_E_L12:
+        out["paper_llr"], out["paper_reweighting"] = PAPER_E_L12[beta]
+    print(json.dumps(out), flush=True)
+
+
 def run_uneven(args):
     """--uneven: lattices of three sizes (L = 8, 12, 16, 64 intervals each over
     E/6V in [0.58, 0.68], dE = 8, 18, 32) in one persistent launch per
@@ -1026,6 +1088,9 @@ def main():
         return
     if args.muca:
         run_muca(args)
+        return
+    if args.canonical:
+        run_canonical(args)
         return
     if args.exchange:
         run_exchange(args)
