@@ -140,6 +140,14 @@ __device__ __forceinline__ void sin_cos(float x, float *s, float *c)
         sincosf(x, s, c);
 }
 
+// arg(x + i y): the polynomial arctangent with fast math, the library's
+// atan2f without.
+template <bool FAST>
+__device__ __forceinline__ float arg(float y, float x)
+{
+    return FAST ? arg_fast(y, x) : atan2f(y, x);
+}
+
 // Coordinates of the h-th site of parity p (lexicographic, x0 fastest).
 __device__ __forceinline__ int decode_half(int h, int p, int L, uint32_t magic, int x[4])
 {
@@ -357,7 +365,7 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, float *th, int p, floa
             const uint32_t link = (uint32_t)MU * V + (uint32_t)site;
             if (von_mises(-a_f * Sabs, link, sweep, tag, k0, k1, cX, sX)) {
                 // theta' = X - alpha, alpha = arg S: e^{i theta'} = e^{iX} conj(S) / |S|
-                thn = atan2f(sX * Sr - cX * Si, cX * Sr + sX * Si);
+                thn = arg<FAST>(sX * Sr - cX * Si, cX * Sr + sX * Si);
                 // dE of the angle actually stored, evaluated exactly like e_old
                 // (same staple sum, same sine/cosine): the approximation errors
                 // of one link's successive evaluations then cancel along its
@@ -481,7 +489,7 @@ __device__ __forceinline__ float overrelax_link(const float *th, const float *ow
     const float t0 = own[h];
     float Sr, Si;
     staple_sum_regs<FAST>(va, Sr, Si);
-    const float tn = wrap_angle(-t0 - 2.0f * atan2f(Si, Sr));
+    const float tn = wrap_angle(-t0 - 2.0f * arg<FAST>(Si, Sr));
     if (WITH_DE) {
         float sn, cn, so, co;
         sin_cos<FAST>(tn, &sn, &cn);

@@ -55,6 +55,33 @@ __device__ __forceinline__ float wrap_angle(float t)
     return t - kTwoPi * floorf((t + kPi) * (1.0f / kTwoPi));
 }
 
+// arg(x + i y) in [-pi, pi] in float32, for the staple direction and the new
+// heat-bath angle.  With t = min(|x|, |y|) / max(|x|, |y|) in [0, 1],
+// atan t = t P(t^2), P the degree-7 polynomial whose t P(t^2) has the least
+// maximum absolute error from atan t on [0, 1] (Remez exchange: 3.7e-8; with
+// float32 coefficients and Horner evaluation 1.4e-7, plus <= 1.2e-7 from the
+// quotient); then the octant: pi/2 - r where |y| > |x|, pi - r where x < 0,
+// the sign of y.  arg(0) = 0.
+__device__ __forceinline__ float arg_fast(float y, float x)
+{
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float t = __fdividef(mn, fmaxf(mx, 1e-30f));
+    const float u = t * t;
+    float p = -0.004054567310959101f;
+    p = fmaf(p, u, 0.021862957626581192f);
+    p = fmaf(p, u, -0.0559123270213604f);
+    p = fmaf(p, u, 0.0964219719171524f);
+    p = fmaf(p, u, -0.1390862911939621f);
+    p = fmaf(p, u, 0.19946566224098206f);
+    p = fmaf(p, u, -0.33329859375953674f);
+    p = fmaf(p, u, 0.9999993443489075f);
+    float r = t * p;
+    r = ay > ax ? 1.57079632679489662f - r : r;
+    r = x < 0.0f ? kPi - r : r;
+    return copysignf(r, y);
+}
+
 // ---------------------------------------------------------------------------
 // Energies on the device are int64 fixed point with 32 fractional bits
 // (resolution 2.3e-10, range +-2.1e9).  Sums are exact and independent of
