@@ -86,9 +86,9 @@ __device__ __forceinline__ bool von_mises(float kappa, uint32_t c0, uint32_t c1,
         return true;
     }
     const float k = fabsf(kappa);
-    const float sq = sqrtf(fmaf(4.0f * k, k, 1.0f));
+    const float sq = sqrt_fast(fmaf(4.0f * k, k, 1.0f));
     const float tau = 1.0f + sq;
-    const float rho = __fdividef(2.0f * k * tau, (sq + 1.0f) * (tau + sqrtf(2.0f * tau)));
+    const float rho = __fdividef(2.0f * k * tau, (sq + 1.0f) * (tau + sqrt_fast(2.0f * tau)));
     const float r = __fdividef(1.0f + rho * rho, 2.0f * rho);
     const float omr = 1.0f - rho;
     const float rm1 = __fdividef(omr * omr, 2.0f * rho);   // r - 1
@@ -122,7 +122,7 @@ __device__ __forceinline__ bool von_mises(float kappa, uint32_t c0, uint32_t c1,
     const float den = r + z;
     const bool pos = 1.0f + r * z >= 0.0f;                   // f >= 0
     const float w = __fdividef(pos ? rm1 * 2.0f * sh * sh : (r + 1.0f) * 2.0f * ch * ch, den);
-    const float s = sqrtf(fmaxf(w * (2.0f - w), 0.0f));
+    const float s = sqrt_fast(w * (2.0f - w));
     const float c = pos ? 1.0f - w : w - 1.0f;
     const bool neg_x = !(w_acc & 1u);                        // X = -acos f
     const bool flip = kappa < 0.0f;                          // X -> X + pi
@@ -360,7 +360,7 @@ __device__ __noinline__ void produce_class(Smem<NWP> &sm, float *th, int p, floa
             float so, co;
             sin_cos<FAST>(t0, &so, &co);
             const float e_old = co * Sr - so * Si;     // |S| cos(theta + alpha)
-            const float Sabs = sqrtf(Sr * Sr + Si * Si);
+            const float Sabs = sqrt_fast(Sr * Sr + Si * Si);
             float cX, sX;
             const uint32_t link = (uint32_t)MU * V + (uint32_t)site;
             if (von_mises(-a_f * Sabs, link, sweep, tag, k0, k1, cX, sX)) {
@@ -1018,13 +1018,13 @@ __device__ __noinline__ void rm_update(LatState &st, const KernelArgs &args, int
     if (args.hist) args.hist[(size_t)step * (size_t)args.n_lat + (size_t)lat] = a_new;
 }
 
-// Resident CTAs per SM the register budget is held to: 128 threads x 8 and
-// 512 threads x 2 (64 registers); 160 threads x 5, 192 threads x 4 and
-// 256 threads x 3 (80 registers).
+// Resident CTAs per SM the register budget is held to: 512 threads x 2 (64
+// registers); 128 threads x 6, 160 threads x 5, 192 threads x 4 and 256
+// threads x 3 (80 registers).
 template <int NWP>
 constexpr int min_ctas()
 {
-    return NWP == 3 ? 8 : NWP == 4 ? 5 : NWP == 5 ? 4 : NWP == 7 ? 3 : 2;
+    return NWP == 3 ? 6 : NWP == 4 ? 5 : NWP == 5 ? 4 : NWP == 7 ? 3 : 2;
 }
 
 template <int NWP, bool FAST>

@@ -55,6 +55,14 @@ __device__ __forceinline__ float wrap_angle(float t)
     return t - kTwoPi * floorf((t + kPi) * (1.0f / kTwoPi));
 }
 
+// sqrt(x) for x >= 0 as x times the hardware reciprocal square root (a few
+// ulp; the sampler's parameters and an angle's sine need no IEEE-rounded
+// sqrtf).  sqrt(0) = 0.
+__device__ __forceinline__ float sqrt_fast(float x)
+{
+    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+}
+
 // arg(x + i y) in [-pi, pi] in float32, for the staple direction and the new
 // heat-bath angle.  With t = min(|x|, |y|) / max(|x|, |y|) in [0, 1],
 // atan t = t P(t^2), P the degree-7 polynomial whose t P(t^2) has the least
