@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--target-intervals", type=int, default=32)
     p.add_argument("--target-replicas", type=int, default=4)
     p.add_argument("--n-rm", type=int, default=150)
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the C0 / C1 / C3 intervals-per-second comparison with the oracle")
     p.add_argument("--physics", action="store_true",
                    help="the paper's volume study at one L (Table 1 parameters): "
                         "beta_c(L) and the specific-heat peak against Table 2 / Table 4")
@@ -430,9 +432,92 @@ def run_ours(args, rank, world, local_rank):
             out["cpu_baseline_1core"], _ = cpu_baseline(w, n_sweeps=1, max_lat=1, threads=1)
         except Exception as e:  # keep the GPU line even if the host baseline fails
             out["cpu_baseline"] = {"error": str(e)}
+    if not args.no_configs and not args.no_cpu and world == 1:
+        out["config_rates"] = config_rates_leg(args, w, value, out.get("cpu_baseline"))
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def config_rates_leg(args, w3, gpu_value, cpu_base):
+    """Intervals per second for whole Robbins-Monro runs (Algorithm 1: hot
+    start, approach, then the configuration's N_RM iterations of every
+    (interval, replica) chain), GPU against the FP64 oracle:
+    - C0: L = 4, 8 intervals x 4 replicas, dE = 4, 50 + 100 sweeps per step,
+      20 steps; both sides run it whole (the oracle one thread per lattice).
+    - C1: L = 8, 32 intervals x 4 replicas, dE = 8, 50 + 100 sweeps per step,
+      100 steps; the GPU runs it whole, the oracle runs 1 and 2 steps of one
+      lattice per host core and is extrapolated from those (labelled so).
+    - C3 (the benchmark, 256 intervals x 8 replicas at L = 20, 200 steps of the
+      timed steps' sweeps): both extrapolated from the measured link-update
+      rates (the GPU's timed value, the oracle's cpu_baseline).
+    An interval counts once all its replicas have finished."""
+    import torch
+    import oracle
+    from paper_1509_08391_gb300 import llr, workloads
+    cores = os.cpu_count() or 1
+    res = {"unit": "intervals/s", "definition": "intervals x replicas whole Robbins-Monro runs "
+           "(approach + N_RM steps); intervals / wall seconds"}
+
+    def gpu_run(w):
+        n = w.n_lattices
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with llr.Batch.from_workload(w, max_approach=w.max_approach) as b:
+            a_dev = torch.full((n,), w.a0, dtype=torch.float64, device="cuda")
+            b.rm_run(a_dev, w.n_therm, w.n_meas, 0, w.n_rm)
+            torch.cuda.synchronize()
+            ok = bool(np.all(b.status() == 0))
+        return time.perf_counter() - t0, ok
+
+    def oracle_run(w, idx, n_rm):
+        L = w.L[idx[0]]
+        g = oracle.Geom([L] * 4)
+        t0 = time.perf_counter()
+        r = oracle.batch_run(g, w.seed, [w.interval_id[i] for i in idx],
+                             [w.replica_id[i] for i in idx], [w.E_lo[i] for i in idx],
+                             [w.dE[i] for i in idx], np.full(len(idx), w.a0), n_or=w.n_or,
+                             block=w.block, n_therm=w.n_therm, n_meas=w.n_meas, n_rm=n_rm,
+                             max_approach=w.max_approach, beta_up=w.beta_up,
+                             beta_dn=w.beta_dn, n_threads=cores)
+        return time.perf_counter() - t0, bool(np.all(r["status"] == 0))
+
+    for name, w in (("C0", workloads.small_l4(replicas=4)), ("C1", workloads.l8_batch(replicas=4))):
+        n_int = len(set(w.interval_id))
+        tg, okg = gpu_run(w)
+        row = {"workload": w.name, "intervals": n_int, "lattices": w.n_lattices,
+               "n_therm": w.n_therm, "n_meas": w.n_meas, "n_rm": w.n_rm,
+               "gpu": {"intervals_per_s": n_int / tg, "seconds": tg, "status_ok": okg}}
+        if name == "C0":
+            to, oko = oracle_run(w, list(range(w.n_lattices)), w.n_rm)
+            row["oracle"] = {"intervals_per_s": n_int / to, "seconds": to, "cores": cores,
+                             "status_ok": oko, "kind": "measured"}
+        else:
+            idx = list(range(min(cores, w.n_lattices)))
+            t1, ok1 = oracle_run(w, idx, 1)
+            t2, ok2 = oracle_run(w, idx, 2)
+            step = max(t2 - t1, 1e-9)
+            t_approach = max(t1 - step, 0.0)
+            waves = -(-w.n_lattices // len(idx))
+            t_all = waves * (t_approach + w.n_rm * step)
+            row["oracle"] = {"intervals_per_s": n_int / t_all, "seconds": t_all, "cores": cores,
+                             "status_ok": ok1 and ok2, "kind": "extrapolated",
+                             "sample": "%d lattices (one per core) for 1 and 2 Robbins-Monro "
+                                       "steps: %.1f s per step, %.1f s approach; x %d steps x %d "
+                                       "waves" % (len(idx), step, t_approach, w.n_rm, waves)}
+        row["gpu_over_oracle"] = row["gpu"]["intervals_per_s"] / row["oracle"]["intervals_per_s"]
+        res[name] = row
+    n3 = len(set(w3.interval_id))
+    upd3 = w3.n_lattices * 200 * (args.n_therm + args.n_meas) * (1 + w3.n_or) * 4 * 20 ** 4
+    c3 = {"workload": w3.name, "intervals": n3, "lattices": w3.n_lattices, "n_rm": 200,
+          "sweeps_per_step": args.n_therm + args.n_meas,
+          "gpu": {"intervals_per_s": n3 / (upd3 / gpu_value), "kind": "extrapolated",
+                  "from": "the timed link-update rate of this line"}}
+    if cpu_base and "value" in cpu_base:
+        c3["oracle"] = {"intervals_per_s": n3 / (upd3 / cpu_base["value"]), "kind": "extrapolated",
+                        "from": "cpu_baseline (%d cores)" % cpu_base.get("cores", cores)}
+    res["C3"] = c3
+    return res
 
 
 def converge_leg(args, L=None, n_int=None, replicas=None, n_rm=None, plain=True):

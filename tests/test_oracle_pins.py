@@ -289,3 +289,48 @@ def test_robbins_monro_step_matches_eq_kk21_on_the_exact_mean():
         err = steps.std(ddof=1) / np.sqrt(steps.size)
         assert abs(steps.mean() - want) < 4 * err + 0.02 * abs(want), (n, steps.mean(), want, err)
         assert 4 * err < 0.25 * abs(want)        # resolves a factor-2 error in the gain
+
+
+def test_robbins_monro_spread_follows_the_asymptotic_variance():
+    """The spread of a_n across independent replicas (Sec. 2.4): for the
+    iteration a <- a + c <<dE>> / (n + 1) with c = 12 / dE^2, near the root
+    <<dE>> has slope -M' in a (M' the window variance of E at the root, by
+    quadrature of eq. (2.15)) and per-step noise sigma^2 (measured at the
+    root), so Var(a_n) -> c^2 sigma^2 / ((2 c M' - 1) n).  Checked on the
+    2-plaquette strip at n = 100 and 400 with 128 replicas: both within the
+    sampling error of a variance (measured ratios ~1.05 and ~0.93), and the 1/n
+    decay between them.  A gain without the 1/(n+1) leaves the spread constant
+    and fails the decay; the gain constant itself is pinned by the one-step
+    test above (a factor 2 moves this variance by only ~1/3)."""
+    lo, hi = 0.5, 1.1
+    dE = hi - lo
+    c = 12.0 / (dE * dE)
+    root = exact2d.llr_root_2plaq(lo, hi)
+    z, s1, s2 = exact2d.restricted_moments_2plaq(lo, hi, root)[:3]
+    Mp = s2 / z - (s1 / z) ** 2
+    assert 2.0 * c * Mp - 1.0 > 0.2          # the regime where the 1/n law holds
+    g = oracle.Geom([3, 2], periodic=False)
+    n_therm, n_meas = 5, 50
+    # sigma^2: variance of one step's <<dE>> estimate at a = root
+    xi = []
+    for r in range(64):
+        t = oracle.Lattice(g, 4242, 5, r, lo, dE, n_or=1, block=1)
+        t.hot_start()
+        assert t.approach(10000) >= 0
+        for k in range(40):
+            a1, m = t.rm_step(root, n_therm, n_meas, 10 ** 9)    # a huge n: a stays put
+            xi.append(m)
+    sigma2 = float(np.var(xi, ddof=1))
+    v_inf = c * c * sigma2 / (2.0 * c * Mp - 1.0)
+    R = 128
+    var = {}
+    for n_rm in (100, 400):
+        out = oracle.batch_run(g, 9090, [0] * R, list(range(R)), [lo] * R, [dE] * R,
+                               [root] * R, n_or=1, block=1, n_therm=n_therm, n_meas=n_meas,
+                               n_rm=n_rm, n_threads=min(8, os.cpu_count() or 1))
+        assert np.all(out["status"] == 0)
+        var[n_rm] = float(np.var(out["a"], ddof=1))
+        # a sample variance of R values has relative sd sqrt(2 / (R - 1)) = 0.125
+        ratio = var[n_rm] / (v_inf / n_rm)
+        assert 0.6 < ratio < 1.5, (n_rm, ratio)
+    assert 0.15 < var[400] / var[100] < 0.45
