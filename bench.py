@@ -430,6 +430,8 @@ def run_ours(args, rank, world, local_rank):
         try:
             out["cpu_baseline"], _ = cpu_baseline(w)
             out["cpu_baseline_1core"], _ = cpu_baseline(w, n_sweeps=1, max_lat=1, threads=1)
+            if not args.no_configs and world == 1:
+                out["cpu_baseline"]["config_rates"] = cpu_baseline_configs()
         except Exception as e:  # keep the GPU line even if the host baseline fails
             out["cpu_baseline"] = {"error": str(e)}
     if not args.no_configs and not args.no_cpu and world == 1:
@@ -440,24 +442,22 @@ def run_ours(args, rank, world, local_rank):
 
 
 def config_rates_leg(args, w3, gpu_value, cpu_base):
-    """Intervals per second for whole Robbins-Monro runs (Algorithm 1: hot
-    start, approach, then the configuration's N_RM iterations of every
-    (interval, replica) chain), GPU against the FP64 oracle:
+    """Intervals per second for whole Robbins-Monro runs on this GPU (Algorithm
+    1: hot start, approach, then the configuration's N_RM iterations of every
+    (interval, replica) chain), set beside the oracle's figures for the same
+    runs that the cpu_baseline leg measured (cpu_base["config_rates"]):
     - C0: L = 4, 8 intervals x 4 replicas, dE = 4, 50 + 100 sweeps per step,
-      20 steps; both sides run it whole (the oracle one thread per lattice).
+      20 steps, run whole;
     - C1: L = 8, 32 intervals x 4 replicas, dE = 8, 50 + 100 sweeps per step,
-      100 steps; the GPU runs it whole, the oracle runs 1 and 2 steps of one
-      lattice per host core and is extrapolated from those (labelled so).
+      100 steps, run whole;
     - C3 (the benchmark, 256 intervals x 8 replicas at L = 20, 200 steps of the
-      timed steps' sweeps): both extrapolated from the measured link-update
-      rates (the GPU's timed value, the oracle's cpu_baseline).
+      timed steps' sweeps): extrapolated from the timed link-update rate.
     An interval counts once all its replicas have finished."""
     import torch
-    import oracle
-    from paper_1509_08391_gb300 import llr, workloads
-    cores = os.cpu_count() or 1
+    from paper_1509_08391_gb300 import llr
     res = {"unit": "intervals/s", "definition": "intervals x replicas whole Robbins-Monro runs "
            "(approach + N_RM steps); intervals / wall seconds"}
+    cpu_rates = (cpu_base or {}).get("config_rates", {})
 
     def gpu_run(w):
         n = w.n_lattices
@@ -470,9 +470,45 @@ def config_rates_leg(args, w3, gpu_value, cpu_base):
             ok = bool(np.all(b.status() == 0))
         return time.perf_counter() - t0, ok
 
+    for name, w in config_workloads():
+        n_int = len(set(w.interval_id))
+        tg, okg = gpu_run(w)
+        row = {"workload": w.name, "intervals": n_int, "lattices": w.n_lattices,
+               "n_therm": w.n_therm, "n_meas": w.n_meas, "n_rm": w.n_rm,
+               "gpu": {"intervals_per_s": n_int / tg, "seconds": tg, "status_ok": okg}}
+        if name in cpu_rates and cpu_rates[name].get("intervals_per_s"):
+            row["gpu_over_cpu_baseline"] = (row["gpu"]["intervals_per_s"]
+                                            / cpu_rates[name]["intervals_per_s"])
+        res[name] = row
+    n3 = len(set(w3.interval_id))
+    upd3 = w3.n_lattices * 200 * (args.n_therm + args.n_meas) * (1 + w3.n_or) * 4 * 20 ** 4
+    c3 = {"workload": w3.name, "intervals": n3, "lattices": w3.n_lattices, "n_rm": 200,
+          "sweeps_per_step": args.n_therm + args.n_meas,
+          "gpu": {"intervals_per_s": n3 / (upd3 / gpu_value), "kind": "extrapolated",
+                  "from": "the timed link-update rate of this line"}}
+    if cpu_base and "value" in cpu_base:
+        c3["cpu_baseline_intervals_per_s"] = n3 / (upd3 / cpu_base["value"])
+        c3["cpu_baseline_kind"] = "extrapolated from cpu_baseline's link-update rate"
+    res["C3"] = c3
+    return res
+
+
+def config_workloads():
+    from paper_1509_08391_gb300 import workloads
+    return (("C0", workloads.small_l4(replicas=4)), ("C1", workloads.l8_batch(replicas=4)))
+
+
+def cpu_baseline_configs():
+    """The oracle's intervals/s for the whole Robbins-Monro runs of C0 and C1
+    (see config_rates_leg), on the host cores, one thread per lattice: C0 run
+    whole; C1 from 1 and 2 steps of one lattice per core, extrapolated to 100
+    steps and all lattices (labelled so)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    out = {}
+
     def oracle_run(w, idx, n_rm):
-        L = w.L[idx[0]]
-        g = oracle.Geom([L] * 4)
+        g = oracle.Geom([w.L[idx[0]]] * 4)
         t0 = time.perf_counter()
         r = oracle.batch_run(g, w.seed, [w.interval_id[i] for i in idx],
                              [w.replica_id[i] for i in idx], [w.E_lo[i] for i in idx],
@@ -482,16 +518,12 @@ def config_rates_leg(args, w3, gpu_value, cpu_base):
                              beta_dn=w.beta_dn, n_threads=cores)
         return time.perf_counter() - t0, bool(np.all(r["status"] == 0))
 
-    for name, w in (("C0", workloads.small_l4(replicas=4)), ("C1", workloads.l8_batch(replicas=4))):
+    for name, w in config_workloads():
         n_int = len(set(w.interval_id))
-        tg, okg = gpu_run(w)
-        row = {"workload": w.name, "intervals": n_int, "lattices": w.n_lattices,
-               "n_therm": w.n_therm, "n_meas": w.n_meas, "n_rm": w.n_rm,
-               "gpu": {"intervals_per_s": n_int / tg, "seconds": tg, "status_ok": okg}}
         if name == "C0":
-            to, oko = oracle_run(w, list(range(w.n_lattices)), w.n_rm)
-            row["oracle"] = {"intervals_per_s": n_int / to, "seconds": to, "cores": cores,
-                             "status_ok": oko, "kind": "measured"}
+            t, ok = oracle_run(w, list(range(w.n_lattices)), w.n_rm)
+            out[name] = {"intervals_per_s": n_int / t, "seconds": t, "cores": cores,
+                         "status_ok": ok, "kind": "measured"}
         else:
             idx = list(range(min(cores, w.n_lattices)))
             t1, ok1 = oracle_run(w, idx, 1)
@@ -500,24 +532,12 @@ def config_rates_leg(args, w3, gpu_value, cpu_base):
             t_approach = max(t1 - step, 0.0)
             waves = -(-w.n_lattices // len(idx))
             t_all = waves * (t_approach + w.n_rm * step)
-            row["oracle"] = {"intervals_per_s": n_int / t_all, "seconds": t_all, "cores": cores,
-                             "status_ok": ok1 and ok2, "kind": "extrapolated",
-                             "sample": "%d lattices (one per core) for 1 and 2 Robbins-Monro "
-                                       "steps: %.1f s per step, %.1f s approach; x %d steps x %d "
-                                       "waves" % (len(idx), step, t_approach, w.n_rm, waves)}
-        row["gpu_over_oracle"] = row["gpu"]["intervals_per_s"] / row["oracle"]["intervals_per_s"]
-        res[name] = row
-    n3 = len(set(w3.interval_id))
-    upd3 = w3.n_lattices * 200 * (args.n_therm + args.n_meas) * (1 + w3.n_or) * 4 * 20 ** 4
-    c3 = {"workload": w3.name, "intervals": n3, "lattices": w3.n_lattices, "n_rm": 200,
-          "sweeps_per_step": args.n_therm + args.n_meas,
-          "gpu": {"intervals_per_s": n3 / (upd3 / gpu_value), "kind": "extrapolated",
-                  "from": "the timed link-update rate of this line"}}
-    if cpu_base and "value" in cpu_base:
-        c3["oracle"] = {"intervals_per_s": n3 / (upd3 / cpu_base["value"]), "kind": "extrapolated",
-                        "from": "cpu_baseline (%d cores)" % cpu_base.get("cores", cores)}
-    res["C3"] = c3
-    return res
+            out[name] = {"intervals_per_s": n_int / t_all, "seconds": t_all, "cores": cores,
+                         "status_ok": ok1 and ok2, "kind": "extrapolated",
+                         "sample": "%d lattices (one per core) for 1 and 2 Robbins-Monro steps: "
+                                   "%.1f s per step, %.1f s approach; x %d steps x %d waves"
+                                   % (len(idx), step, t_approach, w.n_rm, waves)}
+    return out
 
 
 def converge_leg(args, L=None, n_int=None, replicas=None, n_rm=None, plain=True):
