@@ -334,3 +334,32 @@ def test_robbins_monro_spread_follows_the_asymptotic_variance():
         ratio = var[n_rm] / (v_inf / n_rm)
         assert 0.6 < ratio < 1.5, (n_rm, ratio)
     assert 0.15 < var[400] / var[100] < 0.45
+
+
+def test_strong_coupling_slope_in_four_dimensions():
+    """At small E/6V (strong coupling) the 4-D plaquettes are nearly
+    independent: <cos theta_P>(beta) = I1(beta)/I0(beta) up to O(u^5)
+    corrections (u = I1/I0, 4e-5 at u = 0.1), so the slope of ln rho is
+    a(E) = -beta(E) with I1(beta)/I0(beta) = E/6V (appendix, the cumulant
+    form of a_k), up to O(1/V).  Algorithm 1 on the 4^4 lattice at
+    E/6V = 0.05 and 0.10 must land there within its statistical error plus
+    2e-3 (those corrections); a flipped sign, a factor 2 in E or the 1 - cos
+    convention fail it by many errors."""
+    from scipy import optimize, special
+    L, dE, R = 4, 4.0, 4
+    six_v = 6 * L ** 4
+    es = (0.05, 0.10)
+    g = oracle.Geom([L] * 4)
+    lo = [e * six_v - dE / 2 for e in es for _ in range(R)]
+    iid = [k for k in range(len(es)) for _ in range(R)]
+    rid = [r for _ in es for r in range(R)]
+    out = oracle.batch_run(g, 555, iid, rid, lo, [dE] * len(lo), [0.0] * len(lo), n_or=4,
+                           block=1, n_therm=10, n_meas=50, n_rm=100,
+                           n_threads=min(8, os.cpu_count() or 1))
+    assert np.all(out["status"] == 0)
+    a = out["a"].reshape(len(es), R)
+    for k, e in enumerate(es):
+        beta = optimize.brentq(lambda b: special.i1(b) / special.i0(b) - e, 1e-6, 5.0)
+        err = a[k].std(ddof=1) / np.sqrt(R)
+        assert abs(a[k].mean() + beta) < 4 * err + 2e-3, (e, a[k].mean(), -beta, err)
+        assert err < 0.25 * beta          # resolves a factor 2 in the slope
