@@ -344,11 +344,13 @@ def test_strong_coupling_slope_in_four_dimensions():
     form of a_k), up to O(1/V).  Algorithm 1 on the 4^4 lattice at
     E/6V = 0.05 and 0.10 must land there within its statistical error plus
     2e-3 (those corrections); a flipped sign, a factor 2 in E or the 1 - cos
-    convention fail it by many errors."""
+    convention fail it by many errors.  The pi-flux map E -> -E (which the
+    configuration pins check) makes rho(E) = rho(-E), so the slope at
+    E/6V = -0.05 is +beta(0.05): the mirror image at the level of Algorithm 1."""
     from scipy import optimize, special
     L, dE, R = 4, 4.0, 4
     six_v = 6 * L ** 4
-    es = (0.05, 0.10)
+    es = (-0.05, 0.05, 0.10)
     g = oracle.Geom([L] * 4)
     lo = [e * six_v - dE / 2 for e in es for _ in range(R)]
     iid = [k for k in range(len(es)) for _ in range(R)]
@@ -359,7 +361,11 @@ def test_strong_coupling_slope_in_four_dimensions():
     assert np.all(out["status"] == 0)
     a = out["a"].reshape(len(es), R)
     for k, e in enumerate(es):
-        beta = optimize.brentq(lambda b: special.i1(b) / special.i0(b) - e, 1e-6, 5.0)
+        beta = optimize.brentq(lambda b: special.i1(b) / special.i0(b) - abs(e), 1e-6, 5.0)
+        want = -beta if e > 0 else beta
         err = a[k].std(ddof=1) / np.sqrt(R)
-        assert abs(a[k].mean() + beta) < 4 * err + 2e-3, (e, a[k].mean(), -beta, err)
+        assert abs(a[k].mean() - want) < 4 * err + 2e-3, (e, a[k].mean(), want, err)
         assert err < 0.25 * beta          # resolves a factor 2 in the slope
+    # the mirror pair directly
+    err2 = np.hypot(a[0].std(ddof=1), a[1].std(ddof=1)) / np.sqrt(R)
+    assert abs(a[0].mean() + a[1].mean()) < 4 * err2 + 2e-3
