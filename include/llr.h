@@ -278,7 +278,8 @@ int llr_cv_peak(int n, const double *centres, const double *a, double beta_lo, d
  *   E_out, E2_out: host double[n_beta].  Synchronous, default stream; the
  *   call allocates and frees its device buffers (~16 bytes per sample).
  *   Errors: LLR_ERR_ARG (n_samples < 1, n < 1, de <= 0, non-finite e0,
- *   slope or beta, null array), LLR_ERR_CUDA. */
+ *   sample, slope or beta, null array; checked on the host before any device
+ *   work), LLR_ERR_CUDA. */
 int llr_muca_reweight(long long n_samples, const double *E, int n, double e0, double de,
                       const double *a, int n_beta, const double *beta, double *E_out,
                       double *E2_out);

@@ -825,6 +825,8 @@ int muca_samples_init(MucaSamples &w, long long ns, const double *E, int n, doub
     if (ns < 1 || !E) return fail(LLR_ERR_ARG, "need n_samples >= 1 samples");
     if (n < 1 || !a || !std::isfinite(e0) || !std::isfinite(de) || !(de > 0.0))
         return fail(LLR_ERR_ARG, "need n >= 1 finite slopes, finite e0 and de > 0");
+    for (long long i = 0; i < ns; ++i)
+        if (!std::isfinite(E[i])) return fail(LLR_ERR_ARG, "non-finite sample " + std::to_string(i));
     std::vector<double> tab;
     if (int r = muca_table(n, de, a, tab)) return r;
     int dev = 0, sms = 1;

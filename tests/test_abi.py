@@ -54,3 +54,22 @@ def test_reconstruction_rejects_unsorted_centres_without_gpu():
     with pytest.raises(llr.LLRError) as e:
         llr.reconstruct_lnrho([2.0, 1.0], [0.0, 0.0])
     assert e.value.code == llr.LLR_ERR_ARG
+
+
+def test_multicanonical_analysis_rejects_bad_input_without_gpu():
+    """llr_muca_reweight / llr_muca_cv_peak / llr_muca_tunnellings check their
+    arguments on the host before any device work (Sec. 2.6 analysis)."""
+    import numpy as np
+    from paper_1509_08391_gb300 import llr
+    a = np.full(4, -1.0)
+    E = np.linspace(10.0, 20.0, 16)
+    bad = E.copy()
+    bad[3] = np.nan
+    for call in (lambda: llr.muca_reweight(bad, 10.0, 2.5, a, [1.0]),
+                 lambda: llr.muca_reweight(E, 10.0, 0.0, a, [1.0]),
+                 lambda: llr.muca_reweight(E, 10.0, 2.5, a, [np.inf]),
+                 lambda: llr.muca_cv_peak(E, 10.0, 2.5, a, 1.0, 0.5),
+                 lambda: llr.muca_tunnellings(np.zeros((3, 2)), 1.0, -1.0)):
+        with pytest.raises(llr.LLRError) as exc:
+            call()
+        assert exc.value.code == llr.LLR_ERR_ARG
