@@ -30,6 +30,7 @@ METRIC = "link updates/s"
 SFU_OPS_PER_CLK_SM = 16          # special-function (MUFU) ops per SM per clock
 MUFU_PER_UPDATE = 12             # algorithmic: sine and cosine of the 6 staple angles
 BYTES_PER_UPDATE = 8             # algorithmic: read + write one float32 link
+ISSUE_PER_CLK_SM = 4             # warp instructions issued per SM per clock (4 schedulers)
 
 
 def parse():
@@ -258,12 +259,10 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
-def kernel_traffic(lattice_sweeps):
-    """DRAM bytes (read + write) of one launch of the sweep kernel, from the ncu
-    counters committed under profiles/: bytes per lattice-sweep of the captured
-    case times the lattice-sweeps of this launch (the traffic grows in
-    proportion to them).  None when the kernel source has changed since the
-    capture."""
+def kernel_profile():
+    """The ncu record of the sweep kernel committed under profiles/ (DRAM bytes
+    and warp instructions of one captured launch), or None when the kernel
+    source has changed since the capture (SHA-256 check)."""
     import hashlib
     try:
         prof = json.load(open(os.path.join(ROOT, "profiles", "llr_kernel_traffic.json")))
@@ -272,7 +271,39 @@ def kernel_traffic(lattice_sweeps):
         return None
     if prof.get("source_sha256") != hashlib.sha256(src).hexdigest():
         return None
+    return prof
+
+
+def kernel_traffic(lattice_sweeps):
+    """DRAM bytes (read + write) of one launch of the sweep kernel, from the ncu
+    counters committed under profiles/: bytes per lattice-sweep of the captured
+    case times the lattice-sweeps of this launch (the traffic grows in
+    proportion to them).  None when the kernel source has changed since the
+    capture."""
+    prof = kernel_profile()
+    if prof is None:
+        return None
     return float(prof["dram_bytes_per_lattice_sweep"]) * lattice_sweeps
+
+
+def issue_roofline(updates_per_s, n_sm, mhz):
+    """The sweep kernel against the instruction-issue ceiling (4 schedulers per
+    SM, one warp instruction each per clock): warp instructions per link
+    update from the committed ncu capture times the measured update rate.
+    None when the kernel source has changed since the capture."""
+    prof = kernel_profile()
+    if prof is None or "warp_instructions_per_update" not in prof:
+        return None
+    ipu = float(prof["warp_instructions_per_update"])
+    achieved = updates_per_s * ipu / 1e9
+    peak = ISSUE_PER_CLK_SM * n_sm * mhz * 1e6 / 1e9
+    return {"bound": "issue", "achieved": achieved, "peak": peak,
+            "unit": "G warp instructions/s", "frac": achieved / peak,
+            "warp_instructions_per_update": ipu,
+            "peak_source": "%d warp instructions/clk/SM x %d SMs x %.0f MHz (unit counts, the "
+                           "queried SM count and the sampled max clock)"
+                           % (ISSUE_PER_CLK_SM, n_sm, mhz),
+            "instructions_source": "smsp__inst_executed.sum of the committed ncu capture"}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -398,6 +429,7 @@ def run_ours(args, rank, world, local_rank):
         pass
     ach_hbm = BYTES_PER_UPDATE * upd_per_launch / (per_launch_ms / 1e3) / 1e9
     traffic = kernel_traffic(n * (args.n_therm + args.n_meas))
+    issue = issue_roofline(upd_per_launch / (per_launch_ms / 1e3), n_sm, mhz)
     out = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_launch_ms, "higher_is_better": True,
@@ -419,6 +451,7 @@ def run_ours(args, rank, world, local_rank):
                                     "clock)" % (n_sm, mhz)},
         "roofline_hbm": {"bound": "hbm", "achieved": ach_hbm, "peak": hbm_peak, "unit": "GB/s",
                          "frac": ach_hbm / hbm_peak, "peak_source": hbm_src},
+        "roofline_issue": issue,
         "clocks": clk, "gpu_launches": args.steps,
         "e2e": e2e,
     }

@@ -73,3 +73,18 @@ def test_multicanonical_analysis_rejects_bad_input_without_gpu():
         with pytest.raises(llr.LLRError) as exc:
             call()
         assert exc.value.code == llr.LLR_ERR_ARG
+
+
+def test_bench_issue_roofline_arithmetic(monkeypatch):
+    """bench.issue_roofline: warp instructions per update x updates/s against
+    4 warp instructions per SM per clock; None without a matching record."""
+    import bench
+    monkeypatch.setattr(bench, "kernel_profile", lambda: {"warp_instructions_per_update": 10.0})
+    r = bench.issue_roofline(5e10, 152, 2000.0)
+    assert r["bound"] == "issue"
+    assert r["achieved"] == pytest.approx(5e10 * 10.0 / 1e9)
+    assert r["peak"] == pytest.approx(4 * 152 * 2000.0e6 / 1e9)
+    assert r["frac"] == pytest.approx(500.0 / 1216.0)
+    monkeypatch.setattr(bench, "kernel_profile", lambda: None)
+    assert bench.issue_roofline(5e10, 152, 2000.0) is None
+
